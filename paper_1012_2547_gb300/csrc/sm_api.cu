@@ -1,0 +1,800 @@
+// Host side of libsmgpu: the C ABI of include/smgpu.h and include/smgen.h.
+//
+//   sm_prepare*   pattern -> plan: chooses the kernel family (tuning table
+//                 or built-in rule), builds its tables on the host and copies
+//                 them to device memory as one blob.
+//   sm_search*    one query -> workspace reset + one persistent launch.
+//   sm_batch_*    many queries -> descriptors uploaded once; per kernel
+//                 family one persistent launch over all its (query, tile)
+//                 work items; the sequence is captured as a CUDA graph.
+//   sm_tuning_*   the (m bucket, sigma bucket) -> configuration table.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "sm_internal.h"
+#include "smgen.h"
+#include "smgpu.h"
+
+namespace smgpu {
+const void *so_kernel_fn(int kid);
+size_t so_kernel_smem(int kid);
+int so_kernel_threads();
+uint64_t so_tile_starts();
+const void *qg_kernel_fn(int kid);
+int qg_kernel_threads();
+}  // namespace smgpu
+
+using namespace smgpu;
+
+namespace {
+
+constexpr uint32_t kMaxM = 1u << 24;
+constexpr size_t kTicketBytes = 256;  // up to 32 claim counters per launch set
+
+struct DevArena {
+    void *ptr = nullptr;
+    ~DevArena() {
+        if (ptr) cudaFree(ptr);
+    }
+};
+
+struct Workspace {
+    uint8_t *mem = nullptr;
+    size_t bytes = 0;
+};
+
+struct Lib {
+    std::mutex mu;
+    bool inited = false;
+    int device = -1;
+    int sms = 0;
+    uint32_t *err = nullptr;
+    KernelShape shapes[K_COUNT];
+    std::unordered_map<cudaStream_t, Workspace> ws;
+    std::unordered_map<std::string, sm_plan *> cache;
+    sm_config tuning[SM_TUNE_M_BUCKETS * SM_TUNE_S_BUCKETS];
+    std::atomic<uint64_t> launches{0};
+};
+
+Lib &lib() {
+    static Lib *L = new Lib();  // never destroyed: may be used at exit
+    return *L;
+}
+
+sm_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return SM_OK;
+    if (e == cudaErrorMemoryAllocation) return SM_ENOMEM;
+    return SM_ECUDA;
+}
+
+#define SM_TRY_CUDA(expr)                          \
+    do {                                           \
+        cudaError_t e_ = (expr);                   \
+        if (e_ != cudaSuccess) return from_cuda(e_); \
+    } while (0)
+
+// Device init: kernel shapes and the error word.  Caller holds no lock.
+sm_status ensure_init() {
+    Lib &L = lib();
+    std::lock_guard<std::mutex> g(L.mu);
+    if (L.inited) return SM_OK;
+    int dev = 0;
+    SM_TRY_CUDA(cudaGetDevice(&dev));
+    int sms = 0;
+    SM_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    SM_TRY_CUDA(kernels_init(sms));
+    for (int k = 0; k < K_COUNT; ++k) L.shapes[k] = kernel_shape(k);
+    SM_TRY_CUDA(cudaMalloc(&L.err, 256));
+    SM_TRY_CUDA(cudaMemset(L.err, 0, 256));
+    L.device = dev;
+    L.sms = sms;
+    L.inited = true;
+    return SM_OK;
+}
+
+bool aligned8(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
+
+// ---------------------------------------------------------------- plans
+
+uint32_t ceil_log2(uint64_t x) {
+    uint32_t b = 0;
+    while ((1ull << b) < x) ++b;
+    return b;
+}
+
+uint32_t m_bucket(uint32_t m) {
+    uint32_t b = 0;
+    while (b < 11 && (2u << b) <= m) ++b;
+    return b;  // floor(log2 m), capped at 11
+}
+
+uint32_t s_bucket(uint32_t sigma) {
+    if (sigma == 0) return 0;
+    uint32_t b = 0;
+    while (b < 8 && (2u << b) <= sigma) ++b;
+    return std::max(1u, b);  // floor(log2 sigma) in 1..8
+}
+
+uint32_t rule_q(uint32_t m, uint32_t sigma) {
+    const double sg = sigma >= 2 ? static_cast<double>(sigma) : 4.0;
+    int q = static_cast<int>(std::ceil(std::log(64.0 * m) / std::log(sg)));
+    q = std::min(8, std::max(3, q));
+    return std::min<uint32_t>(static_cast<uint32_t>(q), m);
+}
+
+size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+uint64_t pack_qgram(const uint8_t *p, uint32_t q) {
+    uint64_t g = 0;
+    for (uint32_t b = 0; b < q; ++b) g |= static_cast<uint64_t>(p[b]) << (8 * b);
+    return g;
+}
+
+}  // namespace
+
+struct sm_plan {
+    PlanDev hdr;
+    const PlanDev *dev = nullptr;
+    std::shared_ptr<DevArena> arena;
+    int kid = 0;
+    std::vector<uint8_t> pattern;
+};
+
+struct sm_batch {
+    std::shared_ptr<DevArena> arena;  // tickets | states | descriptors | zero list
+    struct Group {
+        int kid;
+        LaunchArgs args;
+        int grid;
+    };
+    std::vector<Group> groups;
+    uint64_t **zero_list = nullptr;
+    uint32_t nzero = 0;
+    size_t reset_bytes = 0;  // tickets + states, zeroed before each launch
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint32_t kernels = 0;
+};
+
+namespace {
+
+// Host blob for one pattern.  Returns SM_EINVAL if `cfg` cannot serve it.
+sm_status build_blob(const uint8_t *p, uint32_t m, uint32_t sigma, const sm_config *cfg,
+                     std::vector<uint8_t> *blob, PlanDev *hdr_out, int *kid_out) {
+    Lib &L = lib();
+    sm_config tc{};
+    {
+        std::lock_guard<std::mutex> g(L.mu);
+        tc = L.tuning[m_bucket(m) * SM_TUNE_S_BUCKETS + s_bucket(sigma)];
+    }
+    uint32_t variant = cfg && cfg->variant ? cfg->variant : tc.variant;
+    if (variant == SM_VARIANT_AUTO) variant = m <= 64 ? SM_VARIANT_SHIFTOR : SM_VARIANT_QGRAM;
+    // A tuned (not explicit) choice that cannot serve m falls back to the rule.
+    const bool explicit_cfg = cfg && cfg->variant;
+    if (!explicit_cfg && variant == SM_VARIANT_SHIFTOR && m > 64) variant = SM_VARIANT_QGRAM;
+    const sm_config *src = explicit_cfg ? cfg : &tc;
+
+    PlanDev h{};
+    h.m = m;
+    int kid = 0;
+    uint32_t q = 0, wb = 0;
+    uint64_t R = 0;
+    if (variant == SM_VARIANT_SHIFTOR) {
+        wb = src->word_bits ? src->word_bits : (m <= 32 ? 32u : 64u);
+        if (!explicit_cfg && m > wb) wb = 64;
+        if ((wb != 32 && wb != 64) || m > wb) return SM_EINVAL;
+        h.hist = wb == 32 ? (m <= 17) : (m <= 49);
+        kid = wb == 32 ? (h.hist ? K_SO32H : K_SO32A) : (h.hist ? K_SO64H : K_SO64A);
+        h.variant = VAR_SHIFTOR;
+        h.word_bits = wb;
+        h.tile_starts = static_cast<uint32_t>(so_tile_starts());
+    } else if (variant == SM_VARIANT_QGRAM) {
+        q = src->q ? src->q : rule_q(m, sigma);
+        if (!explicit_cfg) q = std::min(q, m);
+        if (q < 1 || q > 8 || q > m) return SM_EINVAL;
+        const uint32_t s = m - q + 1;
+        uint32_t ppt = src->tile ? (1u << std::min(src->tile, 20u)) / s : 4096u / s;
+        ppt = std::max(2u, std::min(ppt, 256u));
+        R = static_cast<uint64_t>(ppt) * s;
+        if (R * qg_kernel_threads() >= (1ull << 32)) return SM_EINVAL;
+        h.variant = VAR_QGRAM;
+        h.q = q;
+        h.s = s;
+        h.tile_starts = static_cast<uint32_t>(R * qg_kernel_threads());
+        kid = K_QGRAM;
+    } else if (variant == SM_VARIANT_LINEAR) {
+        R = std::max<uint64_t>(1024, 4ull * m);
+        if (src->tile) R = std::max<uint64_t>(R, 1ull << std::min(src->tile, 24u));
+        if (R * qg_kernel_threads() >= (1ull << 32)) return SM_EINVAL;
+        h.variant = VAR_LINEAR;
+        h.tile_starts = static_cast<uint32_t>(R * qg_kernel_threads());
+        kid = K_LINEAR;
+    } else {
+        return SM_EINVAL;
+    }
+
+    // q-gram table: keys in first-seen order, offsets per key descending.
+    std::vector<uint64_t> keys;
+    std::unordered_map<uint64_t, std::vector<uint32_t>> groups;
+    if (h.variant == VAR_QGRAM) {
+        for (uint32_t j = 0; j + q <= m; ++j) {
+            const uint64_t g = pack_qgram(p + j, q);
+            auto it = groups.find(g);
+            if (it == groups.end()) {
+                keys.push_back(g);
+                groups[g].push_back(j);
+            } else {
+                it->second.push_back(j);
+            }
+        }
+        h.slot_bits = std::max(4u, ceil_log2(2ull * keys.size()));
+        h.bm_bits = std::min(16u, std::max(10u, h.slot_bits + 4));
+    }
+
+    // Layout.
+    size_t off = sizeof(PlanDev);
+    h.off_tbl = static_cast<uint32_t>(off);
+    off += h.variant == VAR_SHIFTOR ? 256 * (wb / 8) : 0;
+    off = align16(off);
+    h.off_pat = static_cast<uint32_t>(off);
+    off += align16(m) + 16;
+    h.off_bitmap = static_cast<uint32_t>(off);
+    off += h.variant == VAR_QGRAM ? (size_t(1) << h.bm_bits) / 8 : 0;
+    off = align16(off);
+    h.off_slots = static_cast<uint32_t>(off);
+    off += h.variant == VAR_QGRAM ? (size_t(1) << h.slot_bits) * sizeof(QSlot) : 0;
+    h.off_offs = static_cast<uint32_t>(off);
+    off += h.variant == VAR_QGRAM ? align16(4ull * (m - q + 1)) : 0;
+    h.off_fail = static_cast<uint32_t>(off);
+    off += align16(4ull * (m + 1));
+    off = (off + 255) & ~size_t(255);
+    if (off >= (1ull << 32)) return SM_EINVAL;
+    h.bytes = static_cast<uint32_t>(off);
+
+    blob->assign(off, 0);
+    uint8_t *b = blob->data();
+    if (h.variant == VAR_SHIFTOR) {
+        // Shift-And masks: bit j of B[c] is 1 iff p[j] = c; bits >= m are 1
+        // so that older match flags survive the AND.
+        const uint64_t low = m >= 64 ? ~0ull : ((1ull << m) - 1);
+        for (int c = 0; c < 256; ++c) {
+            uint64_t w = ~low;
+            for (uint32_t j = 0; j < m; ++j)
+                if (p[j] == c) w |= 1ull << j;
+            if (wb == 32) {
+                const uint32_t w32 = static_cast<uint32_t>(w);
+                std::memcpy(b + h.off_tbl + 4 * c, &w32, 4);
+            } else {
+                std::memcpy(b + h.off_tbl + 8 * c, &w, 8);
+            }
+        }
+    }
+    std::memcpy(b + h.off_pat, p, m);
+    if (h.variant == VAR_QGRAM) {
+        uint32_t *bitmap = reinterpret_cast<uint32_t *>(b + h.off_bitmap);
+        QSlot *slots = reinterpret_cast<QSlot *>(b + h.off_slots);
+        uint32_t *offs = reinterpret_cast<uint32_t *>(b + h.off_offs);
+        const uint32_t mask = (1u << h.slot_bits) - 1;
+        uint32_t next = 0;
+        for (uint64_t g : keys) {
+            const std::vector<uint32_t> &js = groups[g];
+            const uint64_t hh = g * 0x9E3779B97F4A7C15ull;
+            const uint32_t bb = static_cast<uint32_t>(hh >> (64 - h.bm_bits));
+            bitmap[bb >> 5] |= 1u << (bb & 31);
+            uint32_t sl = static_cast<uint32_t>(hh >> (64 - h.slot_bits));
+            while (slots[sl].count) sl = (sl + 1) & mask;
+            slots[sl].key = g;
+            slots[sl].first = next;
+            slots[sl].count = static_cast<uint32_t>(js.size());
+            for (size_t r = js.size(); r-- > 0;) offs[next++] = js[r];  // descending j
+        }
+    }
+    // Border table (Knuth-Morris-Pratt): fail[q] = length of the longest
+    // proper border of p[0..q-1].
+    uint32_t *fail = reinterpret_cast<uint32_t *>(b + h.off_fail);
+    fail[0] = 0;
+    if (m >= 1) fail[1] = 0;
+    uint32_t kk = 0;
+    for (uint32_t i = 1; i < m; ++i) {
+        while (kk > 0 && p[kk] != p[i]) kk = fail[kk];
+        if (p[kk] == p[i]) ++kk;
+        fail[i + 1] = kk;
+    }
+    std::memcpy(b, &h, sizeof(h));
+    *hdr_out = h;
+    *kid_out = kid;
+    return SM_OK;
+}
+
+sm_status prepare_many(const uint8_t *patterns, const uint32_t *lengths, uint32_t count,
+                       uint32_t sigma, const sm_config *cfg, sm_plan **out) {
+    sm_status st = ensure_init();
+    if (st != SM_OK) return st;
+    std::vector<std::vector<uint8_t>> blobs(count);
+    std::vector<PlanDev> hdrs(count);
+    std::vector<int> kids(count);
+    size_t total = 0, pos = 0;
+    std::vector<size_t> offs(count);
+    for (uint32_t i = 0; i < count; ++i) {
+        const uint32_t m = lengths[i];
+        if (m == 0 || m > kMaxM) return SM_EINVAL;
+        st = build_blob(patterns + pos, m, sigma, cfg, &blobs[i], &hdrs[i], &kids[i]);
+        if (st != SM_OK) return st;
+        offs[i] = total;
+        total += blobs[i].size();
+        pos += m;
+    }
+    std::vector<uint8_t> host(total);
+    for (uint32_t i = 0; i < count; ++i) std::memcpy(host.data() + offs[i], blobs[i].data(), blobs[i].size());
+    auto arena = std::make_shared<DevArena>();
+    SM_TRY_CUDA(cudaMalloc(&arena->ptr, std::max<size_t>(total, 256)));
+    SM_TRY_CUDA(cudaMemcpy(arena->ptr, host.data(), total, cudaMemcpyHostToDevice));
+    pos = 0;
+    for (uint32_t i = 0; i < count; ++i) {
+        sm_plan *pl = new sm_plan();
+        pl->hdr = hdrs[i];
+        pl->dev = reinterpret_cast<const PlanDev *>(static_cast<uint8_t *>(arena->ptr) + offs[i]);
+        pl->arena = arena;
+        pl->kid = kids[i];
+        pl->pattern.assign(patterns + pos, patterns + pos + lengths[i]);
+        pos += lengths[i];
+        out[i] = pl;
+    }
+    return SM_OK;
+}
+
+// ---------------------------------------------------------------- launches
+
+// Workspace of at least `bytes` for `stream` (grows; growth synchronises).
+sm_status get_workspace(cudaStream_t stream, size_t bytes, uint8_t **out) {
+    Lib &L = lib();
+    std::lock_guard<std::mutex> g(L.mu);
+    Workspace &w = L.ws[stream];
+    if (w.bytes < bytes) {
+        if (w.mem) cudaFree(w.mem);
+        w.mem = nullptr;
+        w.bytes = 0;
+        const size_t want = std::max<size_t>(bytes, std::max<size_t>(2 * w.bytes, 1 << 20));
+        cudaError_t e = cudaMalloc(&w.mem, want);
+        if (e != cudaSuccess) return from_cuda(e);
+        w.bytes = want;
+    }
+    *out = w.mem;
+    return SM_OK;
+}
+
+int grid_for(int kid, uint64_t tickets) {
+    const KernelShape &s = lib().shapes[kid];
+    const uint64_t full = static_cast<uint64_t>(lib().sms) * std::max(1, s.blocks_per_sm);
+    return static_cast<int>(std::max<uint64_t>(1, std::min(full, tickets)));
+}
+
+bool query_ok(const uint8_t *text, uint64_t n, const sm_plan *plan, const uint64_t *out_pos,
+              uint64_t cap, const uint64_t *out_count) {
+    if (!plan || !out_count || !aligned8(out_count)) return false;
+    if (n > 0 && !text) return false;
+    if (n >= (1ull << 62)) return false;
+    if (cap > 0 && (!out_pos || !aligned8(out_pos))) return false;
+    return true;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- kernels
+
+namespace smgpu {
+
+static KernelShape g_shapes[K_COUNT];
+
+cudaError_t kernels_init(int sms) {
+    (void)sms;
+    for (int k = 0; k < K_COUNT; ++k) {
+        KernelShape &s = g_shapes[k];
+        if (k <= K_SO64A) {
+            s.fn = so_kernel_fn(k);
+            s.threads = so_kernel_threads();
+            s.smem = so_kernel_smem(k);
+            cudaError_t e = cudaFuncSetAttribute(s.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 static_cast<int>(s.smem));
+            if (e != cudaSuccess) return e;
+        } else {
+            s.fn = qg_kernel_fn(k);
+            s.threads = qg_kernel_threads();
+            s.smem = 0;
+        }
+        int bps = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, s.fn, s.threads, s.smem);
+        if (e != cudaSuccess) return e;
+        s.blocks_per_sm = std::max(1, bps);
+    }
+    return cudaSuccess;
+}
+
+const KernelShape &kernel_shape(int kid) { return g_shapes[kid]; }
+
+uint64_t kernel_tile_starts(int kid, const PlanDev &hdr) {
+    return kid <= K_SO64A ? so_tile_starts() : hdr.tile_starts;
+}
+
+uint64_t kernel_ntiles(int kid, const PlanDev &hdr, const uint8_t *text, uint64_t n) {
+    if (n < hdr.m) return 0;
+    const uint64_t T = kernel_tile_starts(kid, hdr);
+    if (kid <= K_SO64A) {
+        const uint64_t o = reinterpret_cast<uintptr_t>(text) & 15u;
+        const uint64_t V = o + n - hdr.m + 1;
+        return (V + T - 1) / T;
+    }
+    return (n - hdr.m + 1 + T - 1) / T;
+}
+
+cudaError_t kernel_launch(int kid, const LaunchArgs &a, int grid, cudaStream_t stream) {
+    const KernelShape &s = g_shapes[kid];
+    void *args[] = {const_cast<LaunchArgs *>(&a)};
+    cudaError_t e = cudaLaunchKernel(s.fn, dim3(grid), dim3(s.threads), args, s.smem, stream);
+    if (e == cudaSuccess) lib().launches.fetch_add(1, std::memory_order_relaxed);
+    return e;
+}
+
+}  // namespace smgpu
+
+// ---------------------------------------------------------------- C ABI
+
+namespace {
+
+sm_status search_plan_impl(const sm_plan *plan, const uint8_t *text, uint64_t n, uint64_t *out_pos,
+                           uint64_t cap, uint64_t *out_count, cudaStream_t stream) {
+    if (!query_ok(text, n, plan, out_pos, cap, out_count)) return SM_EINVAL;
+    sm_status st = ensure_init();
+    if (st != SM_OK) return st;
+    const uint64_t ntiles = kernel_ntiles(plan->kid, plan->hdr, text, n);
+    if (ntiles == 0) {
+        SM_TRY_CUDA(cudaMemsetAsync(out_count, 0, sizeof(uint64_t), stream));
+        return SM_OK;
+    }
+    const size_t bytes = kTicketBytes + ntiles * sizeof(uint64_t);
+    uint8_t *ws = nullptr;
+    st = get_workspace(stream, bytes, &ws);
+    if (st != SM_OK) return st;
+    SM_TRY_CUDA(cudaMemsetAsync(ws, 0, bytes, stream));
+    LaunchArgs a{};
+    a.nq = 1;
+    a.one.text = text;
+    a.one.n = n;
+    a.one.plan = plan->dev;
+    a.one.out_pos = out_pos;
+    a.one.cap = cap;
+    a.one.out_count = out_count;
+    a.one.state = reinterpret_cast<uint64_t *>(ws + kTicketBytes);
+    a.one.ntiles = ntiles;
+    a.one.first_ticket = 0;
+    a.ticket = reinterpret_cast<unsigned long long *>(ws);
+    a.total = ntiles;
+    a.err = lib().err;
+    SM_TRY_CUDA(kernel_launch(plan->kid, a, grid_for(plan->kid, ntiles), stream));
+    return SM_OK;
+}
+
+// Builds the device-side structures of a batch inside `arena` (allocated
+// here) and fills `b` (groups, zero list).  Descriptors are copied with a
+// blocking copy.
+sm_status batch_build(const sm_query *qs, uint32_t nq, sm_batch *b) {
+    for (uint32_t i = 0; i < nq; ++i)
+        if (!query_ok(qs[i].text, qs[i].n, qs[i].plan, qs[i].out_pos, qs[i].cap, qs[i].out_count))
+            return SM_EINVAL;
+    sm_status st = ensure_init();
+    if (st != SM_OK) return st;
+    // Group by kernel, keeping input order inside a group.
+    std::vector<std::vector<uint32_t>> by_kid(K_COUNT);
+    std::vector<uint64_t *> zero;
+    std::vector<uint64_t> ntiles(nq);
+    for (uint32_t i = 0; i < nq; ++i) {
+        ntiles[i] = kernel_ntiles(qs[i].plan->kid, qs[i].plan->hdr, qs[i].text, qs[i].n);
+        if (ntiles[i] == 0) zero.push_back(qs[i].out_count);
+        else by_kid[qs[i].plan->kid].push_back(i);
+    }
+    uint64_t total_states = 0;
+    size_t ndesc = 0;
+    for (int k = 0; k < K_COUNT; ++k)
+        for (uint32_t i : by_kid[k]) {
+            total_states += ntiles[i];
+            ++ndesc;
+        }
+    const size_t states_off = kTicketBytes;
+    const size_t desc_off = align16(states_off + total_states * sizeof(uint64_t));
+    const size_t zero_off = align16(desc_off + ndesc * sizeof(QueryDev));
+    const size_t bytes = zero_off + zero.size() * sizeof(uint64_t *) + 16;
+    auto arena = std::make_shared<DevArena>();
+    SM_TRY_CUDA(cudaMalloc(&arena->ptr, bytes));
+    uint8_t *base = static_cast<uint8_t *>(arena->ptr);
+    std::vector<QueryDev> desc;
+    desc.reserve(ndesc);
+    uint64_t state_pos = 0;
+    int gi = 0;
+    for (int k = 0; k < K_COUNT; ++k) {
+        if (by_kid[k].empty()) continue;
+        const size_t first_desc = desc.size();
+        uint64_t ticket = 0;
+        for (uint32_t i : by_kid[k]) {
+            QueryDev d{};
+            d.text = qs[i].text;
+            d.n = qs[i].n;
+            d.plan = qs[i].plan->dev;
+            d.out_pos = qs[i].out_pos;
+            d.cap = qs[i].cap;
+            d.out_count = qs[i].out_count;
+            d.state = reinterpret_cast<uint64_t *>(base + states_off) + state_pos;
+            d.ntiles = ntiles[i];
+            d.first_ticket = ticket;
+            ticket += ntiles[i];
+            state_pos += ntiles[i];
+            desc.push_back(d);
+        }
+        if (gi >= static_cast<int>(kTicketBytes / 8)) return SM_EINVAL;
+        sm_batch::Group g{};
+        g.kid = k;
+        g.args.qs = reinterpret_cast<const QueryDev *>(base + desc_off) + first_desc;
+        g.args.nq = static_cast<uint32_t>(by_kid[k].size());
+        if (g.args.nq == 1) g.args.one = desc[first_desc];
+        g.args.ticket = reinterpret_cast<unsigned long long *>(base) + gi;
+        g.args.total = ticket;
+        g.args.err = lib().err;
+        g.grid = grid_for(k, ticket);
+        b->groups.push_back(g);
+        ++gi;
+    }
+    if (!desc.empty())
+        SM_TRY_CUDA(cudaMemcpy(base + desc_off, desc.data(), desc.size() * sizeof(QueryDev),
+                               cudaMemcpyHostToDevice));
+    if (!zero.empty())
+        SM_TRY_CUDA(cudaMemcpy(base + zero_off, zero.data(), zero.size() * sizeof(uint64_t *),
+                               cudaMemcpyHostToDevice));
+    b->arena = arena;
+    b->zero_list = reinterpret_cast<uint64_t **>(base + zero_off);
+    b->nzero = static_cast<uint32_t>(zero.size());
+    b->reset_bytes = desc_off;
+    b->kernels = static_cast<uint32_t>(b->groups.size()) + (b->nzero ? 1u : 0u);
+    return SM_OK;
+}
+
+sm_status batch_enqueue(const sm_batch *b, cudaStream_t stream) {
+    SM_TRY_CUDA(cudaMemsetAsync(b->arena->ptr, 0, b->reset_bytes, stream));
+    if (b->nzero) SM_TRY_CUDA(launch_zero_counts(b->zero_list, b->nzero, stream));
+    for (const auto &g : b->groups) SM_TRY_CUDA(kernel_launch(g.kid, g.args, g.grid, stream));
+    return SM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sm_status sm_prepare_ex(const uint8_t *pattern, uint32_t m, uint32_t sigma_hint,
+                        const sm_config *config, sm_stream_t stream, sm_plan **out_plan) {
+    (void)stream;
+    if (!pattern || !out_plan || m == 0 || m > kMaxM) return SM_EINVAL;
+    return prepare_many(pattern, &m, 1, sigma_hint, config, out_plan);
+}
+
+sm_status sm_prepare(const uint8_t *pattern, uint32_t m, uint32_t sigma_hint, sm_stream_t stream,
+                     sm_plan **out_plan) {
+    return sm_prepare_ex(pattern, m, sigma_hint, nullptr, stream, out_plan);
+}
+
+sm_status sm_prepare_many(const uint8_t *patterns, const uint32_t *lengths, uint32_t count,
+                          uint32_t sigma_hint, const sm_config *config, sm_stream_t stream,
+                          sm_plan **out_plans) {
+    (void)stream;
+    if (count == 0) return SM_OK;
+    if (!patterns || !lengths || !out_plans) return SM_EINVAL;
+    return prepare_many(patterns, lengths, count, sigma_hint, config, out_plans);
+}
+
+sm_status sm_plan_free(sm_plan *plan) {
+    delete plan;  // the shared arena is released with its last plan
+    return SM_OK;
+}
+
+sm_status sm_plan_info(const sm_plan *plan, sm_plan_desc *out) {
+    if (!plan || !out) return SM_EINVAL;
+    sm_plan_desc d{};
+    d.m = plan->hdr.m;
+    d.variant = plan->hdr.variant == VAR_SHIFTOR ? SM_VARIANT_SHIFTOR
+                : plan->hdr.variant == VAR_QGRAM ? SM_VARIANT_QGRAM
+                                                 : SM_VARIANT_LINEAR;
+    d.q = plan->hdr.q;
+    d.word_bits = plan->hdr.word_bits;
+    d.hist = plan->hdr.hist;
+    d.tile_starts = static_cast<uint32_t>(kernel_tile_starts(plan->kid, plan->hdr));
+    d.device_bytes = plan->hdr.bytes;
+    *out = d;
+    return SM_OK;
+}
+
+sm_status sm_search_plan(const sm_plan *plan, const uint8_t *text, uint64_t n, uint64_t *out_pos,
+                         uint64_t cap, uint64_t *out_count, sm_stream_t stream) {
+    return search_plan_impl(plan, text, n, out_pos, cap, out_count, stream);
+}
+
+sm_status sm_search(const uint8_t *text, uint64_t n, const uint8_t *pattern, uint32_t m,
+                    uint64_t *out_pos, uint64_t cap, uint64_t *out_count, sm_stream_t stream) {
+    if (!pattern || m == 0 || m > kMaxM) return SM_EINVAL;
+    if (!out_count || !aligned8(out_count) || (n > 0 && !text)) return SM_EINVAL;
+    if (cap > 0 && (!out_pos || !aligned8(out_pos))) return SM_EINVAL;
+    Lib &L = lib();
+    const std::string key(reinterpret_cast<const char *>(pattern), m);
+    sm_plan *plan = nullptr;
+    {
+        std::lock_guard<std::mutex> g(L.mu);
+        auto it = L.cache.find(key);
+        if (it != L.cache.end()) plan = it->second;
+    }
+    if (!plan) {
+        sm_status st = sm_prepare(pattern, m, 0, stream, &plan);
+        if (st != SM_OK) return st;
+        std::lock_guard<std::mutex> g(L.mu);
+        if (L.cache.size() >= 4096) {
+            cudaDeviceSynchronize();  // cached plans may be in use
+            for (auto &kv : L.cache) delete kv.second;
+            L.cache.clear();
+        }
+        auto ins = L.cache.emplace(key, plan);
+        if (!ins.second) {
+            delete plan;
+            plan = ins.first->second;
+        }
+    }
+    return search_plan_impl(plan, text, n, out_pos, cap, out_count, stream);
+}
+
+sm_status sm_search_batch(const sm_query *queries, uint32_t nq, sm_stream_t stream) {
+    if (nq == 0) return SM_OK;
+    if (!queries) return SM_EINVAL;
+    sm_batch b;
+    sm_status st = batch_build(queries, nq, &b);
+    if (st != SM_OK) return st;
+    st = batch_enqueue(&b, stream);
+    if (st != SM_OK) return st;
+    // The batch's device memory must outlive the enqueued work.
+    SM_TRY_CUDA(cudaStreamSynchronize(stream));
+    return SM_OK;
+}
+
+sm_status sm_batch_create(const sm_query *queries, uint32_t nq, uint32_t flags, sm_stream_t stream,
+                          sm_batch **out_batch) {
+    (void)stream;
+    if (!out_batch || (nq > 0 && !queries)) return SM_EINVAL;
+    sm_batch *b = new sm_batch();
+    sm_status st = nq ? batch_build(queries, nq, b) : SM_OK;
+    if (st != SM_OK) {
+        delete b;
+        return st;
+    }
+    if (nq && !(flags & 1u)) {
+        cudaStream_t cs = nullptr;
+        cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            st = batch_enqueue(b, cs);
+            cudaGraph_t graph = nullptr;
+            e = cudaStreamEndCapture(cs, &graph);
+            if (e == cudaSuccess && st == SM_OK) {
+                b->graph = graph;
+                e = cudaGraphInstantiate(&b->exec, graph, 0);
+            }
+            // Capture counted the launches; replays count them again.
+            lib().launches.fetch_sub(b->groups.size(), std::memory_order_relaxed);
+        }
+        if (cs) cudaStreamDestroy(cs);
+        if (e != cudaSuccess || st != SM_OK) {
+            if (b->exec) cudaGraphExecDestroy(b->exec);
+            if (b->graph) cudaGraphDestroy(b->graph);
+            delete b;
+            return st != SM_OK ? st : from_cuda(e);
+        }
+    }
+    *out_batch = b;
+    return SM_OK;
+}
+
+sm_status sm_batch_launch(sm_batch *batch, sm_stream_t stream) {
+    if (!batch) return SM_EINVAL;
+    if (batch->groups.empty() && batch->nzero == 0) return SM_OK;
+    if (batch->exec) {
+        SM_TRY_CUDA(cudaGraphLaunch(batch->exec, stream));
+        lib().launches.fetch_add(batch->groups.size(), std::memory_order_relaxed);
+        return SM_OK;
+    }
+    return batch_enqueue(batch, stream);
+}
+
+sm_status sm_batch_free(sm_batch *batch) {
+    if (!batch) return SM_OK;
+    if (batch->exec) cudaGraphExecDestroy(batch->exec);
+    if (batch->graph) cudaGraphDestroy(batch->graph);
+    delete batch;
+    return SM_OK;
+}
+
+sm_status sm_tuning_set(const sm_config *entries, uint32_t count) {
+    if (!entries || count != SM_TUNE_M_BUCKETS * SM_TUNE_S_BUCKETS) return SM_EINVAL;
+    Lib &L = lib();
+    std::lock_guard<std::mutex> g(L.mu);
+    std::memcpy(L.tuning, entries, sizeof(L.tuning));
+    return SM_OK;
+}
+
+sm_status sm_tuning_get(sm_config *entries, uint32_t count) {
+    if (!entries || count != SM_TUNE_M_BUCKETS * SM_TUNE_S_BUCKETS) return SM_EINVAL;
+    Lib &L = lib();
+    std::lock_guard<std::mutex> g(L.mu);
+    std::memcpy(entries, L.tuning, sizeof(L.tuning));
+    return SM_OK;
+}
+
+sm_status sm_tuning_reset(void) {
+    Lib &L = lib();
+    std::lock_guard<std::mutex> g(L.mu);
+    std::memset(L.tuning, 0, sizeof(L.tuning));
+    return SM_OK;
+}
+
+sm_status sm_sync(sm_stream_t stream) {
+    sm_status st = ensure_init();
+    if (st != SM_OK) return st;
+    SM_TRY_CUDA(cudaStreamSynchronize(stream));
+    uint32_t err = 0;
+    SM_TRY_CUDA(cudaMemcpy(&err, lib().err, sizeof(err), cudaMemcpyDeviceToHost));
+    if (err) {
+        SM_TRY_CUDA(cudaMemset(lib().err, 0, sizeof(err)));
+        return SM_ETIMEOUT;
+    }
+    return SM_OK;
+}
+
+uint64_t sm_kernel_launches(void) { return lib().launches.load(); }
+
+sm_status sm_shutdown(void) {
+    Lib &L = lib();
+    std::lock_guard<std::mutex> g(L.mu);
+    if (!L.inited) return SM_OK;
+    cudaDeviceSynchronize();
+    for (auto &kv : L.ws)
+        if (kv.second.mem) cudaFree(kv.second.mem);
+    L.ws.clear();
+    for (auto &kv : L.cache) delete kv.second;
+    L.cache.clear();
+    return SM_OK;
+}
+
+const char *sm_strerror(sm_status status) {
+    switch (status) {
+        case SM_OK: return "success";
+        case SM_EINVAL: return "invalid argument";
+        case SM_ENOMEM: return "out of memory";
+        case SM_ECUDA: return "CUDA runtime error";
+        case SM_ETIMEOUT: return "bounded device wait timed out";
+        case SM_ETRUNC: return "more occurrences than output capacity";
+    }
+    return "unknown status";
+}
+
+sm_status sm_gen_text(uint8_t *out, uint64_t start, uint64_t count, uint64_t key, uint32_t sigma,
+                      const uint32_t *thresholds, uint32_t nthr, const uint8_t *byte_map,
+                      sm_stream_t stream) {
+    if (count && !out) return SM_EINVAL;
+    if (sigma == 0 && (!thresholds || nthr == 0 || nthr > 255)) return SM_EINVAL;
+    if (sigma > 256) return SM_EINVAL;
+    sm_status st = ensure_init();
+    if (st != SM_OK) return st;
+    SM_TRY_CUDA(launch_gen_text(out, start, count, key, sigma, thresholds, nthr, byte_map, stream));
+    lib().launches.fetch_add(count ? 1 : 0, std::memory_order_relaxed);
+    return SM_OK;
+}
+
+}  // extern "C"

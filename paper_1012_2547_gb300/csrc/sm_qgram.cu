@@ -1,0 +1,319 @@
+// Long patterns: exact q-gram stride filter with warp-cooperative
+// verification, and the per-segment Knuth-Morris-Pratt scan that serves as
+// its linear-time fallback (and as a kernel family of its own).
+//
+// Filter (the Hash-q idea of Fig. 1, with q-grams compared exactly).  Let
+// s = m - q + 1.  Any occurrence [i, i+m-1] contains exactly one position
+// k*s in [i, i+m-q] (s consecutive integers hold one multiple of s), and
+// the q-gram of the text there equals p[j..j+q-1] for j = k*s - i.  So only
+// the text q-grams at multiples of s are looked up in the table of the
+// pattern's q-grams; each listed offset j gives one candidate i = k*s - j,
+// and every occurrence is produced exactly once.  Offsets are stored in
+// decreasing order, so each thread emits candidates in increasing order.
+//
+// Verification: each lane first compares the first bytes of its own
+// candidate; surviving candidates of the warp are then checked one at a
+// time by all 32 lanes together (lane l compares bytes 16l..16l+15 of every
+// 512-byte block) with a ballot deciding the result.
+//
+// Density guard: a warp that spends more than a fixed number of verification
+// rounds per probe (periodic patterns on periodic text, e.g. a^m in a^n)
+// flags the tile, which is then recomputed with the linear scan: per thread,
+// Knuth-Morris-Pratt over its start range plus m-1 bytes, O(range + m).
+//
+// Compaction is the same as in the bit-parallel kernel: per-thread counts,
+// block scan, decoupled look-back, ordered writes.  Per-thread hits are
+// buffered in shared memory; a thread with more hits than the buffer holds
+// recomputes its range in write mode once its output offset is known.
+#include "sm_internal.h"
+
+namespace smgpu {
+
+namespace {
+
+constexpr int QG_THREADS = 128;
+constexpr int QG_HB = 8;              // buffered hits per thread
+constexpr int QG_ROUNDS_PER_PROBE = 4; // density guard budget (warp rounds per probe)
+
+struct QGCtl {
+    unsigned long long ticket;
+    uint64_t excl;
+    uint32_t qi;
+    uint32_t dense;
+    uint64_t tile;
+    uint32_t warp_ex[32];
+    uint32_t ok;
+};
+
+__device__ __forceinline__ uint64_t qgram_hash(uint64_t g) { return g * 0x9E3779B97F4A7C15ull; }
+
+// Bytes t[pos..pos+q-1] packed little-endian; t[pos+q-1] must be in the text.
+__device__ __forceinline__ uint64_t load_qgram(const uint8_t *t, uint64_t pos, uint32_t q) {
+    const uintptr_t addr = reinterpret_cast<uintptr_t>(t) + pos;
+    const uint64_t *w = reinterpret_cast<const uint64_t *>(addr & ~uintptr_t(7));
+    const uint32_t sh = static_cast<uint32_t>(addr & 7u) * 8u;
+    uint64_t g = __ldg(w);
+    if (sh) {
+        g >>= sh;
+        if (sh / 8u + q > 8u) g |= __ldg(w + 1) << (64u - sh);
+    }
+    return q >= 8 ? g : (g & ((1ull << (8u * q)) - 1ull));
+}
+
+struct PlanView {
+    const uint8_t *pat;
+    const uint32_t *bitmap;
+    const QSlot *slots;
+    const uint32_t *offs;
+    const uint32_t *fail;
+    uint32_t m, q, s, bm_bits, slot_bits;
+};
+
+__device__ __forceinline__ PlanView plan_view(const PlanDev *P) {
+    const uint8_t *b = reinterpret_cast<const uint8_t *>(P);
+    PlanView v;
+    v.m = __ldg(&P->m);
+    v.q = __ldg(&P->q);
+    v.s = __ldg(&P->s);
+    v.bm_bits = __ldg(&P->bm_bits);
+    v.slot_bits = __ldg(&P->slot_bits);
+    v.pat = b + __ldg(&P->off_pat);
+    v.bitmap = reinterpret_cast<const uint32_t *>(b + __ldg(&P->off_bitmap));
+    v.slots = reinterpret_cast<const QSlot *>(b + __ldg(&P->off_slots));
+    v.offs = reinterpret_cast<const uint32_t *>(b + __ldg(&P->off_offs));
+    v.fail = reinterpret_cast<const uint32_t *>(b + __ldg(&P->off_fail));
+    return v;
+}
+
+// Looks up q-gram g; returns the number of offsets and their first index.
+__device__ __forceinline__ uint32_t qgram_lookup(const PlanView &v, uint64_t g, uint32_t *first) {
+    const uint64_t h = qgram_hash(g);
+    const uint32_t hb = static_cast<uint32_t>(h >> (64u - v.bm_bits));
+    if (!((__ldg(&v.bitmap[hb >> 5]) >> (hb & 31u)) & 1u)) return 0;
+    const uint32_t mask = (1u << v.slot_bits) - 1u;
+    uint32_t sl = static_cast<uint32_t>(h >> (64u - v.slot_bits));
+    while (true) {
+        const QSlot *S = &v.slots[sl];
+        const uint32_t cnt = __ldg(&S->count);
+        if (cnt == 0) return 0;
+        if (__ldg(&S->key) == g) {
+            *first = __ldg(&S->first);
+            return cnt;
+        }
+        sl = (sl + 1u) & mask;
+    }
+}
+
+// All lanes: does t[0..m-1] equal p[0..m-1]?
+__device__ __forceinline__ bool warp_equal(const uint8_t *t, const uint8_t *p, uint32_t m) {
+    const uint32_t lane = threadIdx.x & 31u;
+    bool bad = false;
+    for (uint32_t off = lane * 16u; off < m; off += 512u) {
+        const uint32_t e = min(off + 16u, m);
+        for (uint32_t b = off; b < e; ++b) bad |= __ldg(t + b) != __ldg(p + b);
+    }
+    return !__any_sync(0xffffffffu, bad);
+}
+
+enum : int { SINK_BUFFER = 0, SINK_WRITE = 1, SINK_DISCARD = 2 };
+
+// Where a thread's hits go: its shared-memory buffer (count pass), the
+// output array at its offset (write pass), or nowhere (a lane that only
+// helps its warp verify).
+struct Sink {
+    int mode;
+    uint64_t *out;
+    uint64_t cap;
+    uint64_t idx;
+    uint32_t *hb;      // shared buffer, column tid, stride QG_THREADS
+    uint32_t cnt;
+
+    __device__ __forceinline__ void put(uint64_t i, uint64_t L) {
+        if (mode == SINK_WRITE) {
+            if (idx < cap) out[idx] = i;
+            ++idx;
+        } else if (mode == SINK_BUFFER && cnt < QG_HB) {
+            hb[cnt * QG_THREADS] = static_cast<uint32_t>(i - L);
+        }
+        ++cnt;
+    }
+};
+
+// q-gram filter over start range [L, min(L+R, n-m+1)).  All lanes of the
+// warp must call it with the same R (trip counts agree).  Returns false if
+// the warp exceeded the verification budget (count mode only).
+__device__ bool qgram_range(const PlanView &v, const uint8_t *text, uint64_t n, uint64_t L,
+                            uint64_t R, Sink &sink, bool guard) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t s = v.s;
+    const uint64_t hi = min(L + R, n - v.m + 1);  // exclusive; L may be >= hi
+    const uint64_t k0 = L / s;                     // L is a multiple of s
+    const uint64_t probes = R / s + 1;
+    const uint32_t pre = min(v.m, 8u);
+    uint64_t rounds = 0;
+    const uint64_t budget = static_cast<uint64_t>(QG_ROUNDS_PER_PROBE) * probes + 32;
+    for (uint64_t pk = 0; pk < probes; ++pk) {
+        const uint64_t pos = (k0 + pk) * s;
+        uint32_t first = 0, count = 0;
+        if (L < hi && pos + v.q <= n) count = qgram_lookup(v, load_qgram(text, pos, v.q), &first);
+        uint32_t c = 0;
+        while (true) {
+            // Next candidate of this lane that lies in range and passes the
+            // prefix check.
+            uint64_t cand = 0;
+            bool have = false;
+            while (c < count) {
+                const uint64_t j = __ldg(&v.offs[first + c]);
+                ++c;
+                if (pos < j) continue;
+                const uint64_t i = pos - j;
+                if (i < L) continue;
+                if (i >= hi) { c = count; break; }
+                bool eq = true;
+                for (uint32_t b = 0; b < pre; ++b) eq &= __ldg(text + i + b) == __ldg(v.pat + b);
+                if (eq) { cand = i; have = true; break; }
+            }
+            unsigned mask = __ballot_sync(0xffffffffu, have);
+            if (!mask) break;
+            rounds += __popc(mask);
+            if (guard && rounds > budget) return false;
+            while (mask) {
+                const int src = __ffs(mask) - 1;
+                mask &= mask - 1u;
+                const uint64_t ic = __shfl_sync(0xffffffffu, cand, src);
+                const bool eq = warp_equal(text + ic, v.pat, v.m);
+                if (eq && lane == static_cast<uint32_t>(src)) sink.put(cand, L);
+            }
+        }
+    }
+    return true;
+}
+
+// Knuth-Morris-Pratt from state 0 at L: occurrences starting in
+// [L, min(L+R, n-m+1)).  fail[q] = longest proper border of p[0..q-1].
+__device__ void linear_range(const PlanView &v, const uint8_t *text, uint64_t n, uint64_t L,
+                             uint64_t R, Sink &sink) {
+    const uint64_t hi = min(L + R, n - v.m + 1);
+    if (L >= hi) return;
+    const uint64_t end = hi + v.m - 1;  // bytes [L, end)
+    uint32_t q = 0;
+    for (uint64_t i = L; i < end; ++i) {
+        const uint8_t c = __ldg(text + i);
+        while (q > 0 && __ldg(v.pat + q) != c) q = __ldg(&v.fail[q]);
+        if (__ldg(v.pat + q) == c) ++q;
+        if (q == v.m) {
+            sink.put(i + 1 - v.m, L);
+            q = __ldg(&v.fail[q]);
+        }
+    }
+}
+
+template <bool QGRAM>
+__global__ void __launch_bounds__(QG_THREADS) qg_kernel(const LaunchArgs a) {
+    constexpr int NW = QG_THREADS / 32;
+    __shared__ QGCtl ctl;
+    __shared__ uint32_t hbuf[QG_HB * QG_THREADS];
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+
+    while (true) {
+        if (tid == 0) {
+            const unsigned long long t = atomicAdd(a.ticket, 1ull);
+            ctl.ticket = t;
+            if (t < a.total) {
+                uint32_t qi;
+                uint64_t k;
+                resolve_ticket(a, t, &qi, &k);
+                ctl.qi = qi;
+                ctl.tile = k;
+            }
+            ctl.dense = QGRAM ? 0u : 1u;
+        }
+        __syncthreads();
+        if (ctl.ticket >= a.total) break;
+        const QueryDev &Q = query_of(a, ctl.qi);
+        const uint64_t k = ctl.tile;
+        const PlanView v = plan_view(Q.plan);
+        const uint64_t R = __ldg(&Q.plan->tile_starts) / QG_THREADS;
+        const uint64_t L = k * R * QG_THREADS + static_cast<uint64_t>(tid) * R;
+        const uint8_t *text = Q.text;
+        const uint64_t n = Q.n;
+
+        // ---- count pass (q-gram filter, or linear scan for dense tiles)
+        Sink sink{SINK_BUFFER, nullptr, 0, 0, hbuf + tid, 0};
+        if (QGRAM) {
+            const bool fine = qgram_range(v, text, n, L, R, sink, true);
+            if (!__all_sync(0xffffffffu, fine) && lane == 0) ctl.dense = 1u;
+        }
+        __syncthreads();
+        const bool dense = ctl.dense != 0;
+        if (dense) {
+            sink.cnt = 0;
+            linear_range(v, text, n, L, R, sink);
+        }
+        const uint32_t cnt = sink.cnt;
+
+        // ---- block scan + look-back
+        uint32_t x = cnt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += y;
+        }
+        if (lane == 31) ctl.warp_ex[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t val = lane < NW ? ctl.warp_ex[lane] : 0u;
+            uint32_t sc = val;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, sc, d);
+                if (lane >= d) sc += y;
+            }
+            const uint32_t total = __shfl_sync(0xffffffffu, sc, 31);
+            if (lane < NW) ctl.warp_ex[lane] = sc - val;
+            bool ok;
+            const uint64_t ex = lookback_exclusive(Q.state, k, total, a.err, &ok);
+            if (lane == 0) {
+                ctl.excl = ex;
+                ctl.ok = ok ? 1u : 0u;
+                if (ok && k + 1 == Q.ntiles) *Q.out_count = ex + total;
+            }
+        }
+        __syncthreads();
+
+        // ---- write pass
+        if (ctl.ok) {
+            const uint64_t base = ctl.excl + ctl.warp_ex[warp] + (x - cnt);
+            const bool over = cnt > QG_HB;
+            if (!over) {
+                for (uint32_t r = 0; r < cnt; ++r) {
+                    const uint64_t idx = base + r;
+                    if (idx < Q.cap) Q.out_pos[idx] = L + hbuf[r * QG_THREADS + tid];
+                }
+            }
+            // Threads whose hits did not fit recompute their range in write
+            // mode; the whole warp joins when the q-gram path needs it.
+            Sink w{over ? SINK_WRITE : SINK_DISCARD, Q.out_pos, Q.cap, base, nullptr, 0};
+            if (dense) {
+                if (over) linear_range(v, text, n, L, R, w);
+            } else if (__any_sync(0xffffffffu, over)) {
+                qgram_range(v, text, n, L, R, w, false);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+const void *qg_kernel_fn(int kid) {
+    if (kid == K_QGRAM) return reinterpret_cast<const void *>(&qg_kernel<true>);
+    if (kid == K_LINEAR) return reinterpret_cast<const void *>(&qg_kernel<false>);
+    return nullptr;
+}
+
+int qg_kernel_threads() { return QG_THREADS; }
+
+}  // namespace smgpu

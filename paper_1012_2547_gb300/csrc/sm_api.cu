@@ -27,6 +27,7 @@ const void *so_kernel_fn(int kid);
 size_t so_kernel_smem(int kid);
 int so_kernel_threads();
 uint64_t so_tile_starts();
+uint32_t so_hit_buffer();
 const void *qg_kernel_fn(int kid);
 int qg_kernel_threads();
 }  // namespace smgpu
@@ -200,6 +201,8 @@ sm_status build_blob(const uint8_t *p, uint32_t m, uint32_t sigma, const sm_conf
         if (!explicit_cfg) q = std::min(q, m);
         if (q < 1 || q > 8 || q > m) return SM_EINVAL;
         const uint32_t s = m - q + 1;
+        // Base range per thread ~4 KiB of start positions; a launch may give
+        // a thread several base ranges (sub_per_item).
         uint32_t ppt = src->tile ? (1u << std::min(src->tile, 20u)) / s : 4096u / s;
         ppt = std::max(2u, std::min(ppt, 256u));
         R = static_cast<uint64_t>(ppt) * s;
@@ -376,6 +379,18 @@ int grid_for(int kid, uint64_t tickets) {
     return static_cast<int>(std::max<uint64_t>(1, std::min(full, tickets)));
 }
 
+// Units per work item for a launch that covers `units` units (staged
+// sub-tiles of the bit-parallel kernels, base ranges of the others): about four work items per resident block, so a
+// large launch gets long work items (their look-backs then find an
+// inclusive predecessor at once) and a small one keeps every block busy.
+uint32_t sub_per_item(int kid, uint64_t units) {
+    const KernelShape &s = lib().shapes[kid];
+    const uint64_t resident = static_cast<uint64_t>(lib().sms) * std::max(1, s.blocks_per_sm);
+    const uint64_t per = units / (4 * resident);
+    const uint64_t cap = 64;
+    return static_cast<uint32_t>(std::max<uint64_t>(1, std::min<uint64_t>(cap, per)));
+}
+
 bool query_ok(const uint8_t *text, uint64_t n, const sm_plan *plan, const uint64_t *out_pos,
               uint64_t cap, const uint64_t *out_count) {
     if (!plan || !out_count || !aligned8(out_count)) return false;
@@ -428,8 +443,7 @@ uint64_t kernel_ntiles(int kid, const PlanDev &hdr, const uint8_t *text, uint64_
     const uint64_t T = kernel_tile_starts(kid, hdr);
     if (kid <= K_SO64A) {
         const uint64_t o = reinterpret_cast<uintptr_t>(text) & 15u;
-        const uint64_t V = o + n - hdr.m + 1;
-        return (V + T - 1) / T;
+        return (o + n + T - 1) / T;  // staged sub-tiles of end positions
     }
     return (n - hdr.m + 1 + T - 1) / T;
 }
@@ -453,11 +467,13 @@ sm_status search_plan_impl(const sm_plan *plan, const uint8_t *text, uint64_t n,
     if (!query_ok(text, n, plan, out_pos, cap, out_count)) return SM_EINVAL;
     sm_status st = ensure_init();
     if (st != SM_OK) return st;
-    const uint64_t ntiles = kernel_ntiles(plan->kid, plan->hdr, text, n);
-    if (ntiles == 0) {
+    const uint64_t units = kernel_ntiles(plan->kid, plan->hdr, text, n);
+    if (units == 0) {
         SM_TRY_CUDA(cudaMemsetAsync(out_count, 0, sizeof(uint64_t), stream));
         return SM_OK;
     }
+    const uint32_t per = sub_per_item(plan->kid, units);
+    const uint64_t ntiles = (units + per - 1) / per;
     const size_t bytes = kTicketBytes + ntiles * sizeof(uint64_t);
     uint8_t *ws = nullptr;
     st = get_workspace(stream, bytes, &ws);
@@ -474,6 +490,8 @@ sm_status search_plan_impl(const sm_plan *plan, const uint8_t *text, uint64_t n,
     a.one.state = reinterpret_cast<uint64_t *>(ws + kTicketBytes);
     a.one.ntiles = ntiles;
     a.one.first_ticket = 0;
+    a.one.nsub = units;
+    a.one.sub_per_item = per;
     a.ticket = reinterpret_cast<unsigned long long *>(ws);
     a.total = ntiles;
     a.err = lib().err;
@@ -493,11 +511,21 @@ sm_status batch_build(const sm_query *qs, uint32_t nq, sm_batch *b) {
     // Group by kernel, keeping input order inside a group.
     std::vector<std::vector<uint32_t>> by_kid(K_COUNT);
     std::vector<uint64_t *> zero;
-    std::vector<uint64_t> ntiles(nq);
+    std::vector<uint64_t> units(nq), ntiles(nq);
+    uint64_t group_units[K_COUNT] = {};
     for (uint32_t i = 0; i < nq; ++i) {
-        ntiles[i] = kernel_ntiles(qs[i].plan->kid, qs[i].plan->hdr, qs[i].text, qs[i].n);
-        if (ntiles[i] == 0) zero.push_back(qs[i].out_count);
-        else by_kid[qs[i].plan->kid].push_back(i);
+        units[i] = kernel_ntiles(qs[i].plan->kid, qs[i].plan->hdr, qs[i].text, qs[i].n);
+        if (units[i] == 0) zero.push_back(qs[i].out_count);
+        else {
+            by_kid[qs[i].plan->kid].push_back(i);
+            group_units[qs[i].plan->kid] += units[i];
+        }
+    }
+    uint32_t group_per[K_COUNT];
+    for (int k = 0; k < K_COUNT; ++k) group_per[k] = sub_per_item(k, group_units[k]);
+    for (uint32_t i = 0; i < nq; ++i) {
+        const uint32_t per = group_per[qs[i].plan->kid];
+        ntiles[i] = (units[i] + per - 1) / per;
     }
     uint64_t total_states = 0;
     size_t ndesc = 0;
@@ -532,6 +560,8 @@ sm_status batch_build(const sm_query *qs, uint32_t nq, sm_batch *b) {
             d.state = reinterpret_cast<uint64_t *>(base + states_off) + state_pos;
             d.ntiles = ntiles[i];
             d.first_ticket = ticket;
+            d.nsub = units[i];
+            d.sub_per_item = group_per[k];
             ticket += ntiles[i];
             state_pos += ntiles[i];
             desc.push_back(d);

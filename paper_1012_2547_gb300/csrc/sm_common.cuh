@@ -48,9 +48,12 @@ struct QueryDev {
     uint64_t *out_pos;
     uint64_t cap;
     uint64_t *out_count;
-    uint64_t *state;        // look-back words, one per tile
-    uint64_t ntiles;
+    uint64_t *state;        // look-back words, one per work item
+    uint64_t ntiles;        // work items of this query
     uint64_t first_ticket;  // tickets [first_ticket, first_ticket + ntiles)
+    uint64_t nsub;          // bit-parallel kernel: staged sub-tiles of the query
+    uint32_t sub_per_item;  // bit-parallel kernel: sub-tiles per work item
+    uint32_t pad;
 };
 
 // Arguments of one persistent launch over a group of queries that share a
@@ -162,12 +165,19 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
 
 // Single-pass decoupled look-back (Merrill and Garland, "Single-pass
 // Parallel Prefix Scan with Decoupled Look-back", 2016), written from the
-// published method.  Called by one full warp of the block that owns tile k
-// of a query once the tile's hit count `agg` is known.  Tiles of a query are
-// claimed in increasing ticket order, so every tile waited on is already
-// owned by a running block and the wait ends.  Returns the number of hits in
-// tiles 0..k-1; `*ok` turns false if a wait ran out or a predecessor failed,
-// in which case the tile is marked failed so successors stop waiting.
+// published method.  Called by one full warp of the block that owns work
+// item k of a query once the item's hit count `agg` is known.  A window is
+// the 32 nearest unread predecessors (one coalesced load per lane).  While
+// a window holds only aggregates the next round reads 8 windows at once, so
+// a far inclusive prefix costs few round trips; a window blocked on an
+// unpublished item backs off exponentially, so spinning warps do not flood
+// L2.  Items of a query are claimed in increasing ticket order, so every
+// item waited on is already owned by a running block and the wait ends.
+// Returns the number of hits in items 0..k-1; `*ok` turns false if a wait
+// ran out or a predecessor failed, in which case the item is marked failed
+// so successors stop waiting.
+constexpr int LB_WINDOWS = 8;
+
 __device__ __forceinline__ uint64_t lookback_exclusive(uint64_t *state, uint64_t k, uint64_t agg,
                                                        uint32_t *err, bool *ok) {
     const int lane = threadIdx.x & 31;
@@ -178,18 +188,51 @@ __device__ __forceinline__ uint64_t lookback_exclusive(uint64_t *state, uint64_t
     }
     if (lane == 0) st_relaxed(&state[k], LB_AGG | agg);
     uint64_t excl = 0;
-    int64_t j = static_cast<int64_t>(k) - 1;
+    int64_t j = static_cast<int64_t>(k) - 1;  // nearest predecessor not yet summed
+    int nwin = 1;
+    uint32_t sleep_ns = 32;
     uint64_t t0 = 0;
     bool timed = false;
     while (true) {
-        const int64_t idx = j - lane;
-        const uint64_t w = idx >= 0 ? ld_relaxed(&state[idx]) : LB_INC;
-        const uint64_t st = w & ~LB_VAL;
-        const unsigned done_mask = __ballot_sync(0xffffffffu, st == LB_INC || st == LB_ERR);
-        const unsigned empty_mask = __ballot_sync(0xffffffffu, st == LB_EMPTY);
-        const int first = done_mask ? __ffs(done_mask) - 1 : 32;
-        const unsigned before = first == 32 ? 0xffffffffu : ((1u << first) - 1u);
-        if (empty_mask & before) {
+        uint64_t w[LB_WINDOWS];
+#pragma unroll
+        for (int i = 0; i < LB_WINDOWS; ++i) {
+            const int64_t idx = j - lane - 32 * i;
+            w[i] = (i < nwin && idx >= 0) ? ld_relaxed(&state[idx]) : LB_INC;
+        }
+        bool found = false, blocked = false, failed = false;
+        int consumed = 0;  // windows summed in full
+        uint64_t part = 0;
+#pragma unroll
+        for (int i = 0; i < LB_WINDOWS; ++i) {
+            if (i < nwin && !found && !blocked) {
+                const uint64_t st = w[i] & ~LB_VAL;
+                const unsigned done = __ballot_sync(0xffffffffu, st == LB_INC || st == LB_ERR);
+                const unsigned empty = __ballot_sync(0xffffffffu, st == LB_EMPTY);
+                const int first = done ? __ffs(done) - 1 : 32;
+                const unsigned before = first == 32 ? 0xffffffffu : ((1u << first) - 1u);
+                if (empty & before) {
+                    blocked = true;
+                } else {
+                    if (lane <= first) part += w[i] & LB_VAL;
+                    if (first < 32) {
+                        found = true;
+                        failed = __shfl_sync(0xffffffffu, st, first) == LB_ERR;
+                    } else {
+                        consumed = i + 1;
+                    }
+                }
+            }
+        }
+        excl += warp_sum_u64(part);
+        if (failed) {
+            if (lane == 0) st_relaxed(&state[k], LB_ERR);
+            *ok = false;
+            return 0;
+        }
+        if (found) break;
+        j -= 32 * consumed;
+        if (blocked) {
             if (!timed) {
                 t0 = global_ns();
                 timed = true;
@@ -201,19 +244,13 @@ __device__ __forceinline__ uint64_t lookback_exclusive(uint64_t *state, uint64_t
                 *ok = false;
                 return 0;
             }
-            __nanosleep(64);
-            continue;
+            __nanosleep(sleep_ns);
+            sleep_ns = min(sleep_ns * 2, 1024u);
+            nwin = 1;
+        } else {
+            nwin = LB_WINDOWS;  // only aggregates so far: read further per round
+            timed = false;
         }
-        const bool failed = first < 32 && (__shfl_sync(0xffffffffu, st, first) == LB_ERR);
-        if (failed) {
-            if (lane == 0) st_relaxed(&state[k], LB_ERR);
-            *ok = false;
-            return 0;
-        }
-        excl += warp_sum_u64(lane <= first ? (w & LB_VAL) : 0ull);
-        if (first < 32) break;
-        j -= 32;
-        timed = false;
     }
     if (lane == 0) st_relaxed(&state[k], LB_INC | ((excl + agg) & LB_VAL));
     return excl;

@@ -35,7 +35,8 @@ const KernelShape &kernel_shape(int kid);
 // Start positions covered by one work item of kernel `kid` for plan `hdr`.
 uint64_t kernel_tile_starts(int kid, const PlanDev &hdr);
 
-// Number of work items for a query (0 when m > n).
+// Work units of a query (0 when m > n): staged sub-tiles for the
+// bit-parallel kernels, base ranges (tile_starts positions) otherwise.
 uint64_t kernel_ntiles(int kid, const PlanDev &hdr, const uint8_t *text, uint64_t n);
 
 // Persistent launch of kernel `kid` over `a` with `grid` blocks.

@@ -235,7 +235,8 @@ __global__ void __launch_bounds__(QG_THREADS) qg_kernel(const LaunchArgs a) {
         const QueryDev &Q = query_of(a, ctl.qi);
         const uint64_t k = ctl.tile;
         const PlanView v = plan_view(Q.plan);
-        const uint64_t R = __ldg(&Q.plan->tile_starts) / QG_THREADS;
+        const uint64_t R = static_cast<uint64_t>(__ldg(&Q.plan->tile_starts) / QG_THREADS) *
+                           Q.sub_per_item;
         const uint64_t L = k * R * QG_THREADS + static_cast<uint64_t>(tid) * R;
         const uint8_t *text = Q.text;
         const uint64_t n = Q.n;

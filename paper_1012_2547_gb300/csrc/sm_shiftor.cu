@@ -9,59 +9,50 @@
 // and an occurrence ends at e iff bit m-1 of D is 1 (it starts at e-m+1).
 //
 // GB300 mapping
-//   * A persistent block claims work items (query, tile) from a device
-//     counter.  A tile is T = THREADS * S start positions; its T + 64 bytes
-//     are staged HBM -> shared memory by one cp.async.bulk (TMA 1-D copy)
-//     completing on an mbarrier, double-buffered so the next tile streams in
-//     while this one is scanned.
-//   * Thread `tid` scans its own S = 16 * SEGC bytes plus up to 16*HCMAX
-//     bytes of the next segment (the m-1 byte halo), 16 bytes per 128-bit
-//     shared load.  S is an odd multiple of 16 bytes, so the eight lanes of
-//     each quarter-warp read eight different 16-byte bank groups.
+//   * One warp per block; ~16 blocks per SM.  A warp claims work items
+//     (query, item) from a device counter; an item is `sub_per_item`
+//     consecutive sub-tiles of 32 * 144 end positions whose bytes (plus the
+//     64 bytes before them) are staged HBM -> shared memory by one
+//     cp.async.bulk (TMA 1-D copy) on an mbarrier, double-buffered so the
+//     next sub-tile streams in while this one is scanned.
+//   * Lane l scans its own 144-byte segment from the empty state, one
+//     128-bit shared load per 16 bytes (144 is an odd multiple of 16, so the
+//     eight lanes of a quarter-warp hit eight different bank groups).  As
+//     the segment is at least m bytes long, the lane's final state is exact;
+//     lane l+1 takes it (shuffle) and extends only the partial matches it
+//     carries across the boundary, which usually dies within a byte or two.
+//     So no lane re-reads an m-1 byte halo.
 //   * When bits m..m+15 of the state are spare (32-bit state and m <= 17,
 //     64-bit state and m <= 49), B[c] has ones there, so those bits carry
 //     the match flags of the last 16 positions: one shift per 16 bytes
 //     yields all 16 flags (variant "H").  Otherwise the state is ORed into
 //     an accumulator and a chunk with a match is re-scanned (variant "A").
-//   * Per-thread counts -> warp shuffle scan -> block scan -> decoupled
-//     look-back across the tiles of the query -> every thread writes its
-//     hits in increasing order at its global offset (capped by `cap`).
+//   * Per-lane counts -> warp scan -> hits buffered per item in shared
+//     memory -> decoupled look-back across the items of the query ->
+//     coalesced copy to the output (capped by `cap`).
 //
-// Text positions are handled in a "virtual" frame shifted by
-// o = text & 15, so every tile starts on a 16-byte boundary in memory.
+// Positions are handled in a "virtual" frame shifted by o = text & 15, so
+// every staged sub-tile starts on a 16-byte boundary in memory.
 #include "sm_internal.h"
 
 namespace smgpu {
 
 namespace {
 
-constexpr int SO_THREADS = 128;
-constexpr int SO_SEGC = 15;  // chunks of 16 bytes per thread segment (odd)
+constexpr int SO_SEGC = 9;                 // 16-byte chunks per lane segment (odd)
+constexpr int SO_S = SO_SEGC * 16;          // 144 bytes per lane (>= m for m <= 64)
+constexpr uint32_t SO_T = 32 * SO_S;        // end positions per sub-tile (one warp)
+constexpr uint32_t SO_LHALO = 64;           // bytes staged before the sub-tile (>= m-1)
+constexpr uint32_t SO_BUF = SO_LHALO + SO_T;
+constexpr int SO_HITS = 512;                // hits of one work item kept in shared memory
 
-template <typename Word, int THREADS, int SEGC>
-struct SOCfg {
-    static constexpr int S = SEGC * 16;
-    static constexpr uint32_t T = THREADS * S;
-    static constexpr uint32_t HALO = 64;  // >= m-1 for m <= 64, multiple of 16
-    static constexpr uint32_t BUF = T + HALO;
-    static constexpr uint32_t TBL = 256 * sizeof(Word);
+template <typename Word>
+struct SOLayout {
+    static constexpr uint32_t TBL_OFF = 2 * SO_BUF;
+    static constexpr uint32_t HITS_OFF = TBL_OFF + 256 * sizeof(Word);
+    static constexpr uint32_t BAR_OFF = HITS_OFF + SO_HITS * 4;
+    static constexpr uint32_t BYTES = BAR_OFF + 16;
 };
-
-struct SOCtl {
-    uint64_t bar[2];
-    unsigned long long ticket[2];
-    uint64_t tile[2];
-    uint32_t qi[2];
-    uint64_t excl;
-    uint32_t warp_ex[32];
-    uint32_t tile_total;
-    uint32_t ok;
-};
-
-template <typename Word, int THREADS, int SEGC>
-constexpr size_t so_smem_bytes() {
-    return 2 * SOCfg<Word, THREADS, SEGC>::BUF + SOCfg<Word, THREADS, SEGC>::TBL + sizeof(SOCtl);
-}
 
 template <typename Word>
 __device__ __forceinline__ void so_step4(Word &D, uint32_t x, const Word *__restrict__ tbl) {
@@ -86,7 +77,7 @@ __device__ __noinline__ uint32_t so_chunk_flags(Word D, const uint8_t *chunk, co
     return f;
 }
 
-// Bits r of a chunk starting at segment byte cb whose end e = cb + 15 - r
+// Bits r of a chunk starting at segment byte cb whose position cb + 15 - r
 // lies in [elo, ehi).
 __device__ __forceinline__ uint32_t range_mask16(int cb, int elo, int ehi) {
     const int lo = max(cb + 16 - ehi, 0);
@@ -95,198 +86,310 @@ __device__ __forceinline__ uint32_t range_mask16(int cb, int elo, int ehi) {
     return ((2u << hi) - 1u) & ~((1u << lo) - 1u);
 }
 
-template <typename Word, int THREADS, int SEGC>
-__device__ __forceinline__ void so_claim(const LaunchArgs &a, SOCtl &ctl, int b, uint8_t *bufs) {
-    using C = SOCfg<Word, THREADS, SEGC>;
-    const unsigned long long t = atomicAdd(a.ticket, 1ull);
-    ctl.ticket[b] = t;
-    if (t >= a.total) return;
-    uint32_t qi;
-    uint64_t k;
-    resolve_ticket(a, t, &qi, &k);
-    ctl.qi[b] = qi;
-    ctl.tile[b] = k;
-    const QueryDev &Q = query_of(a, qi);
-    const uint64_t o = reinterpret_cast<uintptr_t>(Q.text) & 15u;
-    const uint8_t *base = Q.text - o;
-    const uint64_t vstart = k * static_cast<uint64_t>(C::T);
-    const uint64_t vlim = (o + Q.n + 15u) & ~uint64_t(15);
-    const uint64_t vend = min(vstart + C::BUF, vlim);
-    const uint32_t bytes = static_cast<uint32_t>(vend - vstart);
-    fence_proxy_async_smem();
-    mbar_arrive_expect_tx(&ctl.bar[b], bytes);
-    bulk_g2s(bufs + b * C::BUF, base + vstart, bytes, &ctl.bar[b]);
+// Local scan of one lane segment from the empty state.  F[c] bit r flags an
+// occurrence ending at segment byte 16c + 15 - r; returns the final state,
+// which is exact because the segment is at least m bytes long.
+template <typename Word, bool HIST>
+__device__ __forceinline__ Word so_local(const uint8_t *seg, const Word *tbl, uint32_t m,
+                                         uint32_t (&F)[SO_SEGC]) {
+    Word D = 0;
+#pragma unroll
+    for (int c = 0; c < SO_SEGC; ++c) {
+        const uint4 w = *reinterpret_cast<const uint4 *>(seg + 16 * c);
+        if (HIST) {
+            so_step4(D, w.x, tbl);
+            so_step4(D, w.y, tbl);
+            so_step4(D, w.z, tbl);
+            so_step4(D, w.w, tbl);
+            F[c] = static_cast<uint32_t>(D >> (m - 1)) & 0xFFFFu;
+        } else {
+            const Word Ds = D;
+            Word A = 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t x = q == 0 ? w.x : q == 1 ? w.y : q == 2 ? w.z : w.w;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const uint32_t ch = __byte_perm(x, 0u, 0x4440u | b);
+                    D = ((D << 1) | Word(1)) & tbl[ch];
+                    A |= D;
+                }
+            }
+            F[c] = ((A >> (m - 1)) & Word(1)) ? so_chunk_flags<Word>(Ds, seg + 16 * c, tbl, m) : 0u;
+        }
+    }
+    return D;
 }
 
-template <typename Word, bool HIST, int HCMAX, int THREADS, int SEGC>
-__global__ void __launch_bounds__(THREADS) so_kernel(const LaunchArgs a) {
-    using C = SOCfg<Word, THREADS, SEGC>;
-    constexpr int S = C::S;
-    constexpr int NCH = SEGC + HCMAX;
-    constexpr int NW = THREADS / 32;
-    extern __shared__ __align__(128) uint8_t smem[];
-    uint8_t *bufs = smem;
-    Word *tbl = reinterpret_cast<Word *>(smem + 2 * C::BUF);
-    SOCtl &ctl = *reinterpret_cast<SOCtl *>(smem + 2 * C::BUF + C::TBL);
-    const int tid = threadIdx.x;
-    const int lane = tid & 31;
-    const int warp = tid >> 5;
-
-    if (tid == 0) {
-        mbar_init(&ctl.bar[0], 1);
-        mbar_init(&ctl.bar[1], 1);
-        fence_mbar_init();
-        so_claim<Word, THREADS, SEGC>(a, ctl, 0, bufs);
+// Occurrences that start before the segment and end in its first m-1
+// bytes.  X holds the partial matches inherited from the true state before
+// the segment (bits 0..m-2); they are extended byte by byte until none
+// survives.  Flags are merged into F; returns nothing.
+template <typename Word>
+__device__ __forceinline__ void so_fixup(const uint8_t *seg, const Word *tbl, uint32_t m, Word Dprev,
+                                         uint32_t (&F)[SO_SEGC]) {
+    const Word pm = (Word(1) << (m - 1)) - Word(1);
+    Word X = Dprev & pm;
+    if (!X) return;
+    uint64_t extra = 0;
+    for (uint32_t b = 0; X && b + 1 < m; ++b) {
+        X = (X << 1) & tbl[seg[b]];
+        extra |= static_cast<uint64_t>((X >> (m - 1)) & Word(1)) << b;
+        X &= pm;
     }
-    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < 4 && c < SO_SEGC; ++c)
+        F[c] |= __brev(static_cast<uint32_t>(extra >> (16 * c)) & 0xFFFFu) >> 16;
+}
+
+// State after the m-1 bytes that end at `p` (exclusive), from empty.
+template <typename Word>
+__device__ __forceinline__ Word so_warm(const uint8_t *p, const Word *tbl, uint32_t m) {
+    Word D = 0;
+    for (uint32_t b = 0; b + 1 < m; ++b) D = ((D << 1) | Word(1)) & tbl[p[b]];
+    return D;
+}
+
+// Keep positions e in [elo, ehi) of the segment and count them.
+__device__ __forceinline__ uint32_t so_mask_count(uint32_t (&F)[SO_SEGC], int elo, int ehi) {
+    uint32_t cnt = 0;
+    if (ehi <= elo) {
+#pragma unroll
+        for (int c = 0; c < SO_SEGC; ++c) F[c] = 0u;
+        return 0;
+    }
+    const bool full = elo == 0 && ehi == SO_S;
+#pragma unroll
+    for (int c = 0; c < SO_SEGC; ++c) {
+        if (!full) F[c] &= range_mask16(16 * c, elo, ehi);
+        cnt += __popc(F[c]);
+    }
+    return cnt;
+}
+
+__device__ __forceinline__ uint32_t warp_excl_scan(uint32_t v, uint32_t *total) {
+    const int lane = threadIdx.x & 31;
+    uint32_t x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    *total = __shfl_sync(0xffffffffu, x, 31);
+    return x - v;
+}
+
+// Stage sub-tile s (end positions [s*T, (s+1)*T) in the virtual frame) plus
+// the 64 bytes before it into buffer `dst`.  Lane 0 only.
+__device__ __forceinline__ void so_issue(uint8_t *dst, uint64_t *bar, const QueryDev &Q, uint64_t s) {
+    const uint64_t o = reinterpret_cast<uintptr_t>(Q.text) & 15u;
+    const uint8_t *base = Q.text - o;
+    const uint64_t a = s * static_cast<uint64_t>(SO_T);
+    const uint64_t lo = a >= SO_LHALO ? a - SO_LHALO : 0;
+    const uint64_t vlim = (o + Q.n + 15u) & ~uint64_t(15);
+    const uint64_t hi = min(a + SO_T, vlim);
+    const uint32_t bytes = static_cast<uint32_t>(hi - lo);
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(bar, bytes);
+    bulk_g2s(dst + (SO_LHALO - (a - lo)), base + lo, bytes, bar);
+}
+
+__device__ __forceinline__ bool so_claim(const LaunchArgs &a, unsigned long long *t, uint32_t *qi,
+                                         uint64_t *k) {
+    *t = atomicAdd(a.ticket, 1ull);
+    if (*t >= a.total) return false;
+    resolve_ticket(a, *t, qi, k);
+    return true;
+}
+
+// One warp per block.  The warp claims work items (query, item); an item
+// is `sub_per_item` consecutive sub-tiles of 32 * 144 end positions, staged
+// by bulk copies through a double buffer.  Per sub-tile every lane scans
+// its 144 bytes from the empty state, then patches the occurrences that
+// cross into its segment from the exact state of the previous segment
+// (previous lane, previous sub-tile, or a warm-up over the 64 staged bytes
+// before the item).  Hits of an item are buffered, the item's offset comes
+// from a decoupled look-back, and the buffer is copied out coalesced; an
+// item with more hits than the buffer holds is rescanned and written
+// directly.
+template <typename Word, bool HIST>
+__global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchArgs a) {
+    using L = SOLayout<Word>;
+    extern __shared__ __align__(128) uint8_t smem[];
+    Word *tbl = reinterpret_cast<Word *>(smem + L::TBL_OFF);
+    uint32_t *hits = reinterpret_cast<uint32_t *>(smem + L::HITS_OFF);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L::BAR_OFF);
+    const int lane = threadIdx.x;
+
+    unsigned long long t = 0;
+    uint32_t qi = 0;
+    uint64_t k = 0;
+    if (lane == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+        if (so_claim(a, &t, &qi, &k)) {
+            const QueryDev &Q = query_of(a, qi);
+            so_issue(smem, &bar[0], Q, k * Q.sub_per_item);
+        }
+    }
+    __syncwarp();
+    t = __shfl_sync(0xffffffffu, t, 0);
+    qi = __shfl_sync(0xffffffffu, qi, 0);
+    k = __shfl_sync(0xffffffffu, k, 0);
 
     const PlanDev *cur_plan = nullptr;
     uint32_t m = 1;
     uint32_t parity = 0;  // bit b: parity of the next phase of bar[b]
-    int cur = 0;
-    while (true) {
-        const unsigned long long t = ctl.ticket[cur];
-        if (t >= a.total) break;
-        const uint32_t qi = ctl.qi[cur];
-        const uint64_t k = ctl.tile[cur];
+    int cur = 0;          // buffer holding the next sub-tile to scan
+    unsigned long long nt = 0;
+    uint32_t nqi = 0;
+    uint64_t nk = 0;
+    while (t < a.total) {
         const QueryDev &Q = query_of(a, qi);
         const PlanDev *P = Q.plan;
         if (P != cur_plan) {
             const Word *src = reinterpret_cast<const Word *>(reinterpret_cast<const uint8_t *>(P) +
                                                              __ldg(&P->off_tbl));
-            for (int c = tid; c < 256; c += THREADS) tbl[c] = src[c];
+            for (int c = lane; c < 256; c += 32) tbl[c] = src[c];
             cur_plan = P;
             m = __ldg(&P->m);
+            __syncwarp();
         }
-        __syncthreads();
-        if (tid == 0) so_claim<Word, THREADS, SEGC>(a, ctl, cur ^ 1, bufs);
+        const uint64_t sb = k * Q.sub_per_item;
+        const uint64_t se = min(sb + Q.sub_per_item, Q.nsub);
+        const int64_t o = static_cast<int64_t>(reinterpret_cast<uintptr_t>(Q.text) & 15u);
+        const int64_t vlo = o + static_cast<int64_t>(m) - 1;  // first valid end
+        const int64_t vhi = o + static_cast<int64_t>(Q.n);    // one past the last
+        const int64_t ivstart = static_cast<int64_t>(sb) * SO_T;
 
-        const bool arrived = mbar_wait_bounded(&ctl.bar[cur], (parity >> cur) & 1u);
-        parity ^= 1u << cur;
-        if (!__syncthreads_and(arrived)) {
-            // The tile never arrived: fail it and the prefetched one, wait
-            // (bounded) for the prefetch copy, and leave.
-            if (tid == 0) {
+        // ---- pass over the item's sub-tiles: count and buffer hits
+        uint32_t count = 0;
+        Word carry = 0;
+        bool failed = false;
+        for (uint64_t s = sb; s < se; ++s) {
+            if (lane == 0) {
+                uint8_t *nb = smem + (cur ^ 1) * SO_BUF;
+                if (s + 1 < se) {
+                    so_issue(nb, &bar[cur ^ 1], Q, s + 1);
+                } else if (so_claim(a, &nt, &nqi, &nk)) {
+                    const QueryDev &Qn = query_of(a, nqi);
+                    so_issue(nb, &bar[cur ^ 1], Qn, nk * Qn.sub_per_item);
+                }
+            }
+            const bool arrived = mbar_wait_bounded(&bar[cur], (parity >> cur) & 1u);
+            parity ^= 1u << cur;
+            if (!__all_sync(0xffffffffu, arrived)) {
+                failed = true;
+                break;
+            }
+            const uint8_t *buf = smem + cur * SO_BUF + SO_LHALO;
+            if (s == sb && s > 0 && lane == 0) carry = so_warm(buf - (m - 1), tbl, m);
+            const uint8_t *seg = buf + lane * SO_S;
+            uint32_t F[SO_SEGC];
+            const Word Dend = so_local<Word, HIST>(seg, tbl, m, F);
+            Word Dprev = __shfl_up_sync(0xffffffffu, Dend, 1);
+            if (lane == 0) Dprev = carry;
+            so_fixup(seg, tbl, m, Dprev, F);
+            carry = __shfl_sync(0xffffffffu, Dend, 31);
+            const int64_t x = static_cast<int64_t>(s) * SO_T + lane * SO_S;
+            const int elo = static_cast<int>(vlo - x > 0 ? vlo - x : int64_t(0));
+            const int ehi = static_cast<int>(vhi - x < SO_S ? vhi - x : int64_t(SO_S));
+            const uint32_t cnt = so_mask_count(F, elo, ehi);
+            uint32_t total;
+            const uint32_t ex = warp_excl_scan(cnt, &total);
+            if (cnt && count + total <= SO_HITS) {
+                uint32_t idx = count + ex;
+                const uint32_t rel0 = static_cast<uint32_t>(x - ivstart);
+#pragma unroll
+                for (int c = 0; c < SO_SEGC; ++c) {
+                    uint32_t f = F[c];
+                    while (f) {
+                        const int r = 31 - __clz(f);
+                        f ^= 1u << r;
+                        hits[idx++] = rel0 + 16 * c + 15 - r;
+                    }
+                }
+            }
+            count += total;
+            __syncwarp();  // buffer `cur` and the hit buffer are settled
+            cur ^= 1;
+        }
+        nt = __shfl_sync(0xffffffffu, nt, 0);
+        nqi = __shfl_sync(0xffffffffu, nqi, 0);
+        nk = __shfl_sync(0xffffffffu, nk, 0);
+        if (failed) {
+            if (lane == 0) {
                 atomicOr(a.err, ERR_COPY);
                 st_relaxed(&Q.state[k], LB_ERR);
-                const unsigned long long t2 = ctl.ticket[cur ^ 1];
-                if (t2 < a.total) {
-                    const QueryDev &Q2 = query_of(a, ctl.qi[cur ^ 1]);
-                    st_relaxed(&Q2.state[ctl.tile[cur ^ 1]], LB_ERR);
-                    mbar_wait_bounded(&ctl.bar[cur ^ 1], (parity >> (cur ^ 1)) & 1u);
+                if (nt < a.total) {
+                    const QueryDev &Qn = query_of(a, nqi);
+                    st_relaxed(&Qn.state[nk], LB_ERR);
+                    mbar_wait_bounded(&bar[cur ^ 1], (parity >> (cur ^ 1)) & 1u);
                 }
             }
             return;
         }
 
-        // ---- scan this thread's segment
-        const uint8_t *seg = bufs + cur * C::BUF + tid * S;
-        const int64_t o = static_cast<int64_t>(reinterpret_cast<uintptr_t>(Q.text) & 15u);
-        const int64_t V = o + static_cast<int64_t>(Q.n) - static_cast<int64_t>(m) + 1;
-        const int64_t base = static_cast<int64_t>(k) * C::T + static_cast<int64_t>(tid) * S;
-        const int lo_s = static_cast<int>(o - base > 0 ? o - base : int64_t(0));
-        const int hi_s = static_cast<int>(V - base < S ? V - base : int64_t(S));
-        const uint32_t hc = (m + 14u) >> 4;  // halo chunks: ceil((m-1)/16)
-
-        uint32_t F[NCH];
-        Word D = 0;
+        // ---- item prefix (decoupled look-back), then output
+        bool ok;
+        const uint64_t excl = lookback_exclusive(Q.state, k, count, a.err, &ok);
+        if (ok && lane == 0 && k + 1 == Q.ntiles) *Q.out_count = excl + count;
+        const uint64_t cap = Q.cap;
+        uint64_t *out = Q.out_pos;
+        const int64_t shift = static_cast<int64_t>(m) - 1 + o;  // end -> real start
+        if (ok && count <= SO_HITS) {
+            for (uint32_t r = lane; r < count; r += 32) {
+                const uint64_t idx = excl + r;
+                if (idx < cap) out[idx] = static_cast<uint64_t>(ivstart + hits[r] - shift);
+            }
+        } else if (ok && excl < cap) {
+            // Too many hits to buffer: rescan the item in the free buffer and
+            // write each sub-tile's hits at their final offsets.
+            const int wb = cur ^ 1;
+            uint64_t run = excl;
+            carry = 0;
+            for (uint64_t s = sb; s < se && run < cap; ++s) {
+                if (lane == 0) so_issue(smem + wb * SO_BUF, &bar[wb], Q, s);
+                const bool arrived = mbar_wait_bounded(&bar[wb], (parity >> wb) & 1u);
+                parity ^= 1u << wb;
+                if (!__all_sync(0xffffffffu, arrived)) {
+                    if (lane == 0) atomicOr(a.err, ERR_COPY);
+                    break;
+                }
+                const uint8_t *buf = smem + wb * SO_BUF + SO_LHALO;
+                if (s == sb && s > 0 && lane == 0) carry = so_warm(buf - (m - 1), tbl, m);
+                const uint8_t *seg = buf + lane * SO_S;
+                uint32_t F[SO_SEGC];
+                const Word Dend = so_local<Word, HIST>(seg, tbl, m, F);
+                Word Dprev = __shfl_up_sync(0xffffffffu, Dend, 1);
+                if (lane == 0) Dprev = carry;
+                so_fixup(seg, tbl, m, Dprev, F);
+                carry = __shfl_sync(0xffffffffu, Dend, 31);
+                const int64_t x = static_cast<int64_t>(s) * SO_T + lane * SO_S;
+                const int elo = static_cast<int>(vlo - x > 0 ? vlo - x : int64_t(0));
+                const int ehi = static_cast<int>(vhi - x < SO_S ? vhi - x : int64_t(SO_S));
+                const uint32_t cnt = so_mask_count(F, elo, ehi);
+                uint32_t total;
+                uint64_t idx = run + warp_excl_scan(cnt, &total);
 #pragma unroll
-        for (int c = 0; c < NCH; ++c) {
-            if (c < SEGC || static_cast<uint32_t>(c - SEGC) < hc) {
-                const uint4 w = *reinterpret_cast<const uint4 *>(seg + 16 * c);
-                if (HIST) {
-                    so_step4(D, w.x, tbl);
-                    so_step4(D, w.y, tbl);
-                    so_step4(D, w.z, tbl);
-                    so_step4(D, w.w, tbl);
-                    F[c] = static_cast<uint32_t>(D >> (m - 1)) & 0xFFFFu;
-                } else {
-                    const Word Ds = D;
-                    Word A = 0;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const uint32_t x = q == 0 ? w.x : q == 1 ? w.y : q == 2 ? w.z : w.w;
-#pragma unroll
-                        for (int b = 0; b < 4; ++b) {
-                            const uint32_t ch = __byte_perm(x, 0u, 0x4440u | b);
-                            D = ((D << 1) | Word(1)) & tbl[ch];
-                            A |= D;
-                        }
+                for (int c = 0; c < SO_SEGC; ++c) {
+                    uint32_t f = F[c];
+                    while (f) {
+                        const int r = 31 - __clz(f);
+                        f ^= 1u << r;
+                        if (idx < cap) out[idx] = static_cast<uint64_t>(x + 16 * c + 15 - r - shift);
+                        ++idx;
                     }
-                    F[c] = ((A >> (m - 1)) & Word(1)) ? so_chunk_flags<Word>(Ds, seg + 16 * c, tbl, m)
-                                                       : 0u;
                 }
-            } else {
-                F[c] = 0u;
+                run += total;
+                __syncwarp();
             }
         }
-
-        // ---- keep ends e in [lo_s + m - 1, hi_s + m - 1) and count
-        uint32_t cnt = 0;
-        if (hi_s <= lo_s) {
-#pragma unroll
-            for (int c = 0; c < NCH; ++c) F[c] = 0u;
-        } else {
-            const int elo = lo_s + static_cast<int>(m) - 1;
-            const int ehi = hi_s + static_cast<int>(m) - 1;
-            const bool full = lo_s == 0 && hi_s == S;
-#pragma unroll
-            for (int c = 0; c < NCH; ++c) {
-                if (!full || c >= SEGC) F[c] &= range_mask16(16 * c, elo, ehi);
-                cnt += __popc(F[c]);
-            }
-        }
-
-        // ---- block scan of counts
-        uint32_t x = cnt;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
-            if (lane >= d) x += y;
-        }
-        if (lane == 31) ctl.warp_ex[warp] = x;
-        __syncthreads();
-        if (warp == 0) {
-            uint32_t v = lane < NW ? ctl.warp_ex[lane] : 0u;
-            uint32_t s = v;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, s, d);
-                if (lane >= d) s += y;
-            }
-            const uint32_t total = __shfl_sync(0xffffffffu, s, 31);
-            if (lane < NW) ctl.warp_ex[lane] = s - v;
-            bool ok;
-            const uint64_t ex = lookback_exclusive(Q.state, k, total, a.err, &ok);
-            if (lane == 0) {
-                ctl.excl = ex;
-                ctl.tile_total = total;
-                ctl.ok = ok ? 1u : 0u;
-                if (ok && k + 1 == Q.ntiles) *Q.out_count = ex + total;
-            }
-        }
-        __syncthreads();
-
-        // ---- write hits in increasing order
-        if (cnt != 0 && ctl.ok) {
-            uint64_t idx = ctl.excl + ctl.warp_ex[warp] + (x - cnt);
-            const uint64_t cap = Q.cap;
-            uint64_t *out = Q.out_pos;
-            const int64_t rbase = base - o - static_cast<int64_t>(m) + 1;
-#pragma unroll
-            for (int c = 0; c < NCH; ++c) {
-                uint32_t f = F[c];
-                while (f) {
-                    const int r = 31 - __clz(f);
-                    f ^= 1u << r;
-                    const uint64_t pos = static_cast<uint64_t>(rbase + 16 * c + 15 - r);
-                    if (idx < cap) out[idx] = pos;
-                    ++idx;
-                }
-            }
-        }
-        __syncthreads();
-        cur ^= 1;
+        __syncwarp();
+        t = nt;
+        qi = nqi;
+        k = nk;
     }
 }
 
@@ -294,25 +397,24 @@ __global__ void __launch_bounds__(THREADS) so_kernel(const LaunchArgs a) {
 
 // ---------------------------------------------------------------- registry
 
-#define SO_INST(W, H, HC) so_kernel<W, H, HC, SO_THREADS, SO_SEGC>
-
 const void *so_kernel_fn(int kid) {
     switch (kid) {
-        case K_SO32H: return reinterpret_cast<const void *>(&SO_INST(uint32_t, true, 1));
-        case K_SO32A: return reinterpret_cast<const void *>(&SO_INST(uint32_t, false, 2));
-        case K_SO64H: return reinterpret_cast<const void *>(&SO_INST(uint64_t, true, 3));
-        case K_SO64A: return reinterpret_cast<const void *>(&SO_INST(uint64_t, false, 4));
+        case K_SO32H: return reinterpret_cast<const void *>(&so_kernel<uint32_t, true>);
+        case K_SO32A: return reinterpret_cast<const void *>(&so_kernel<uint32_t, false>);
+        case K_SO64H: return reinterpret_cast<const void *>(&so_kernel<uint64_t, true>);
+        case K_SO64A: return reinterpret_cast<const void *>(&so_kernel<uint64_t, false>);
         default: return nullptr;
     }
 }
 
 size_t so_kernel_smem(int kid) {
-    return (kid == K_SO32H || kid == K_SO32A) ? so_smem_bytes<uint32_t, SO_THREADS, SO_SEGC>()
-                                              : so_smem_bytes<uint64_t, SO_THREADS, SO_SEGC>();
+    return (kid == K_SO32H || kid == K_SO32A) ? SOLayout<uint32_t>::BYTES : SOLayout<uint64_t>::BYTES;
 }
 
-int so_kernel_threads() { return SO_THREADS; }
+int so_kernel_threads() { return 32; }
 
-uint64_t so_tile_starts() { return SOCfg<uint32_t, SO_THREADS, SO_SEGC>::T; }
+uint64_t so_tile_starts() { return SO_T; }
+
+uint32_t so_hit_buffer() { return SO_HITS; }
 
 }  // namespace smgpu

@@ -1,0 +1,539 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 exact string matching library.
+
+Default workload (the paper-shaped sweep): ten 4 MiB synthetic texts shaped
+like the paper's text buffers (Section 2), m in {2, 4, ..., 1024}, 100
+substring patterns per (text, m): 10,000 searches = 41.9 GB scanned per
+step.  A step runs every search once, as one persistent, graph-captured
+launch per kernel family (sm_batch_launch), with plans and texts resident in
+HBM.  L2 is flushed (a 256 MiB write) before every timed step, outside the
+timed events.
+
+Prints ONE JSON line (rank 0):
+  metric/value      scanned text GB/s (sum of n over all searches / step time)
+  roofline          dominant kernel family: algorithmic bytes (n per search +
+                    8 bytes per reported position) / its mean launch time,
+                    against the measured HBM copy bandwidth
+  e2e               the same metric through the C ABI from pinned host
+                    buffers: texts H2D, sm_prepare_many, sm_search_batch,
+                    positions D2H, all inside the timed region
+  cpu_baseline      the CPU oracle (naive definition) on a bounded sample
+  clocks            nvidia-smi samples taken during the timed region
+
+--impl reference times the CPU oracle (the reference arm of this tier) on a
+bounded sample of the same workload.  --workload bandwidth runs the 8 GiB
+single-pattern scans (Section 2's bandwidth-style run at GB300 scale);
+--workload single the 1 MiB single search.
+
+Multi-GPU (--gpus N under torchrun): every rank runs the full per-GPU
+workload on its own GPU (independent replicas, weak scaling); the step time
+is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+FALLBACK_HBM_GBS = 6800.0
+L2_FLUSH_BYTES = 256 << 20
+
+
+# ---------------------------------------------------------------- helpers
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """Max of a float over all ranks (identity for world == 1)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def source_hash() -> str:
+    """Hash of the CUDA sources (ties committed ncu traffic to a build)."""
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1012_2547_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel: str):
+    """dram read+write bytes per launch from profiles/traffic.txt when it was
+    taken on the current sources, else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None, None
+    cur = source_hash()
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        kv = dict(x.split("=", 1) for x in line.split() if "=" in x)
+        if kv.get("kernel") == kernel and kv.get("source") == cur:
+            return float(kv["bytes_per_launch"]), kv.get("units_per_launch")
+    return None, None
+
+
+# ---------------------------------------------------------------- CPU oracle timing
+
+def cpu_sample_time(texts, queries, budget_s: float, threads: int):
+    """Time the oracle (threaded naive) on a deterministic sample of the
+    queries, stopping after ~budget_s seconds.  Returns (bytes, seconds,
+    searches)."""
+    import oracle
+    lib = oracle.load()
+    done_b, done_n = 0, 0
+    t0 = time.perf_counter()
+    order = list(range(len(queries)))
+    # spread the sample over texts and lengths
+    step = max(1, len(order) // 997)
+    sample = order[::step] + [i for i in order if i % step]
+    for qi in sample:
+        q = queries[qi]
+        t = texts[q.text_id]
+        n = len(t) if q.n is None else q.n
+        oracle.count_mt(t[:n], q.pattern, threads=threads, lib=lib)
+        done_b += n
+        done_n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    return done_b, time.perf_counter() - t0, done_n
+
+
+# ---------------------------------------------------------------- our arm
+
+def family_key(plan) -> tuple:
+    i = plan.info()
+    return (i.variant, i.word_bits, i.hist)
+
+
+def family_name(key) -> str:
+    v, wb, hist = key
+    if v == "shiftor":
+        return f"so_kernel<u{wb},{'H' if hist else 'A'}>"
+    return {"qgram": "qg_kernel<qgram>", "linear": "qg_kernel<linear>"}.get(v, v)
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    if rank == 0 or world > 1:
+        __graft_entry__.build()
+    import paper_1012_2547_gb300 as smg
+    from paper_1012_2547_gb300 import workloads
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    if args.workload == "sweep":
+        w = workloads.sweep()
+    elif args.workload == "single":
+        w = workloads.single()
+    else:
+        raise SystemExit("--workload bandwidth is driven by bench_bandwidth() below")
+    texts_h = w.texts
+    texts_d = [torch.from_numpy(t).to(dev) for t in texts_h]
+    queries = w.queries
+    nq = len(queries)
+
+    # plans, grouped by sigma hint to keep the tuning buckets right
+    plans = [None] * nq
+    by_sigma = {}
+    for i, q in enumerate(queries):
+        by_sigma.setdefault(q.sigma_hint, []).append(i)
+    for sg, idx in by_sigma.items():
+        ps = smg.prepare_many([queries[i].pattern for i in idx], sigma_hint=sg)
+        for i, p in zip(idx, ps):
+            plans[i] = p
+
+    # count pass (sizes the outputs), then exact output buffers
+    counts = torch.zeros(nq, dtype=torch.int64, device=dev)
+    items = [(texts_d[q.text_id], plans[i], None, counts[i:i + 1]) for i, q in enumerate(queries)]
+    smg.search_batch(items)
+    smg.sync()
+    cnt_h = counts.cpu().numpy()
+    total_hits = int(cnt_h.sum())
+    outbuf = torch.empty(max(total_hits, 1), dtype=torch.int64, device=dev)
+    offs = np.concatenate([[0], np.cumsum(cnt_h)])
+
+    fam = {}
+    for i in range(nq):
+        fam.setdefault(family_key(plans[i]), []).append(i)
+    batches = []
+    for key, idx in sorted(fam.items()):
+        its = [(texts_d[queries[i].text_id], plans[i],
+                outbuf[int(offs[i]):int(offs[i + 1])], counts[i:i + 1]) for i in idx]
+        alg = sum(len(texts_h[queries[i].text_id]) for i in idx) + 8 * int(cnt_h[idx].sum())
+        batches.append({"key": key, "batch": smg.Batch(its, graph=True), "alg_bytes": alg,
+                        "n": len(idx), "times": []})
+
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in batches]
+
+    def step(record: bool):
+        for b, (e0, e1) in zip(batches, ev):
+            e0.record(stream)
+            b["batch"].launch(stream)
+            e1.record(stream)
+        if record:
+            torch.cuda.synchronize()
+            for b, (e0, e1) in zip(batches, ev):
+                b["times"].append(e0.elapsed_time(e1) / 1e3)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step(False)
+    torch.cuda.synchronize()
+    smg.sync()
+    for b in batches:
+        b["times"].clear()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    launches0 = smg.kernel_launches()
+    step_times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        step(True)
+        step_times.append(sum(b["times"][-1] for b in batches))
+    torch.cuda.synchronize()
+    launches = smg.kernel_launches() - launches0
+    barrier(world)
+    clk = clocks.stop()
+    smg.sync()
+
+    per_step = sum(step_times) / len(step_times)
+    per_step_max = max_over_ranks(per_step, world, dev)
+    scanned = w.scanned_bytes
+    value = world * scanned / per_step_max / 1e9
+
+    # parity sample (outside the timed region)
+    import oracle
+    rng = np.random.default_rng(0)
+    sample = sorted(set(rng.integers(0, nq, 12).tolist()) | {0, nq - 1})
+    parity_ok = True
+    for i in sample:
+        q = queries[i]
+        got = outbuf[int(offs[i]):int(offs[i + 1])].cpu().numpy().astype(np.uint64)
+        exp = oracle.kmp(texts_h[q.text_id], q.pattern) if len(q.pattern) > 64 else \
+            oracle.naive_mt(texts_h[q.text_id], q.pattern)
+        parity_ok &= bool(np.array_equal(got, exp))
+
+    # roofline: dominant family
+    hbm, peak_kind = peaks()
+    dom = max(batches, key=lambda b: statistics.mean(b["times"]))
+    dom_t = statistics.mean(dom["times"])
+    achieved = dom["alg_bytes"] / dom_t / 1e9
+    kname = family_name(dom["key"])
+    traffic, _ = committed_traffic(kname + ":" + w.name)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "traffic": traffic, "kernel": kname,
+                "peak_kind": peak_kind, "kernel_ms": round(dom_t * 1e3, 4),
+                "kernel_share": round(dom_t / per_step, 4),
+                "families": {family_name(b["key"]): {"searches": b["n"],
+                                                      "ms": round(statistics.mean(b["times"]) * 1e3, 4)}
+                             for b in batches}}
+
+    # e2e through the C ABI from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        pinned = [torch.from_numpy(t).pin_memory() for t in texts_h]
+        outs_h = torch.empty(max(total_hits, 1), dtype=torch.int64).pin_memory()
+        cnts_h = torch.empty(nq, dtype=torch.int64).pin_memory()
+        h2d = sum(len(t) for t in texts_h)
+        e2e_times = []
+        plan_bytes = 0
+        for r in range(max(1, args.e2e_steps) + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for td, th in zip(texts_d, pinned):
+                td.copy_(th, non_blocking=True)
+            pl = [None] * nq
+            for sg, idx in by_sigma.items():
+                ps = smg.prepare_many([queries[i].pattern for i in idx], sigma_hint=sg)
+                for i, p in zip(idx, ps):
+                    pl[i] = p
+            its = [(texts_d[q.text_id], pl[i], outbuf[int(offs[i]):int(offs[i + 1])], counts[i:i + 1])
+                   for i, q in enumerate(queries)]
+            smg.search_batch(its)
+            outs_h.copy_(outbuf, non_blocking=True)
+            cnts_h.copy_(counts, non_blocking=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            if r > 0:
+                e2e_times.append(dt)
+            plan_bytes = sum(p.info().device_bytes for p in pl)
+            for p in pl:
+                p.free()
+        e2e_t = max_over_ranks(statistics.mean(e2e_times), world, dev)
+        e2e = {"value": round(world * scanned / e2e_t / 1e9, 2), "unit": "GB/s",
+               "h2d_bytes_per_step": int(h2d + plan_bytes),
+               "d2h_bytes_per_step": int(8 * total_hits + 8 * nq),
+               "ms_per_step": round(e2e_t * 1e3, 3)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        b, s, k = cpu_sample_time(texts_h, queries, args.cpu_seconds, threads)
+        cpu = {"value": round(b / s / 1e9, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
+               "sample": f"{k} of {nq} sweep searches ({b / 1e9:.2f} GB), threaded naive"}
+
+    return {
+        "metric": "scanned text GB/s (% of HBM peak) per sigma,m",
+        "value": round(value, 2),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(per_step_max * 1e3, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": w.name, "searches": nq, "scanned_bytes_per_step": scanned,
+                   "positions_per_step": total_hits, "l2": "flushed (256 MiB write) before each step",
+                   "parallelism": f"replicas{world}"},
+        "pct_of_hbm_peak": round(100 * value / world / hbm, 2),
+        "roofline": roofline,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+        "gpu_launches": int(launches),
+        "parity_sample": {"searches": len(sample), "ok": parity_ok},
+    }
+
+
+# ---------------------------------------------------------------- bandwidth workload
+
+def bench_bandwidth(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1012_2547_gb300 as smg
+    from paper_1012_2547_gb300 import gen, workloads
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    n = args.bw_bytes
+    w = workloads.bandwidth(n=n)
+    spec = w.specs[0]
+    text = torch.empty(n, dtype=torch.uint8, device=dev)
+    smg.gen_text(text, 0, spec.key, 4)
+    # dense stress region: a^n-dominated first 64 MiB
+    dense = workloads.bandwidth_dense()
+    pre = min(workloads.DENSE_PREFIX, n)
+    host_pre = spec.window(0, pre).copy()
+    gen.plant_prefix(host_pre, pre, 4096, seed=77)
+    text[:pre].copy_(torch.from_numpy(host_pre))
+    smg.sync()
+    queries = w.queries + dense
+    plans = smg.prepare_many([q.pattern for q in queries], sigma_hint=4)
+    cnt = torch.zeros(len(queries), dtype=torch.int64, device=dev)
+    for i, q in enumerate(queries):
+        smg.search_into(text, plans[i], None, cnt[i:i + 1], n=q.n or n, cap=0)
+    smg.sync()
+    caps = cnt.cpu().numpy()
+    outs = [torch.empty(max(int(c), 1), dtype=torch.int64, device=dev) for c in caps]
+    res = []
+    for i, q in enumerate(queries):
+        nn = q.n or n
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ts = []
+        for r in range(args.warmup + args.steps):
+            e0.record(stream)
+            smg.search_into(text, plans[i], outs[i], cnt[i:i + 1], n=nn, cap=int(caps[i]))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if r >= args.warmup:
+                ts.append(e0.elapsed_time(e1) / 1e3)
+        t = statistics.median(ts)
+        res.append({"m": len(q.pattern), "n": nn, "hits": int(caps[i]), "ms": round(t * 1e3, 4),
+                    "GBs": round(nn / t / 1e9, 1), "variant": plans[i].info().variant})
+    hbm, kind = peaks()
+    print(json.dumps({"workload": w.name, "peak_gbs": hbm, "peak_kind": kind, "results": res}))
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(args, world, rank):
+    """The reference arm of this tier: the CPU oracle on the host cores."""
+    from paper_1012_2547_gb300 import workloads
+    w = workloads.sweep() if args.workload == "sweep" else workloads.single()
+    threads = os.cpu_count() or 1
+    budget = max(1.0, args.ref_seconds / max(1, args.steps + args.warmup))
+    times = []
+    sample_bytes = 0
+    for r in range(args.warmup + args.steps):
+        b, s, k = cpu_sample_time(w.texts, w.queries, budget, threads)
+        if r >= args.warmup:
+            times.append(s / b)
+            sample_bytes = b
+    per_byte = statistics.mean(times)
+    value = 1.0 / per_byte / 1e9
+    scanned = w.scanned_bytes
+    return {
+        "impl": "reference",
+        "metric": "scanned text GB/s (% of HBM peak) per sigma,m",
+        "value": round(value, 4), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(per_byte * scanned * 1e3, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": w.name, "searches": len(w.queries), "scanned_bytes_per_step": scanned},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
+                         "sample": f"~{sample_bytes / 1e9:.2f} GB of the sweep per step, threaded naive"},
+        "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["sweep", "single", "bandwidth"], default="sweep")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=60.0)
+    ap.add_argument("--bw-bytes", type=int, default=8 << 30)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, world, rank)), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    try:
+        if args.workload == "bandwidth":
+            if rank == 0:
+                bench_bandwidth(args, world, rank, local)
+            return
+        out = run_ours(args, world, rank, local)
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -105,12 +105,14 @@ typedef struct {
     uint64_t *hits;
     uint64_t count, alloc;
     int failed;
+    int want_hits;
 } chunk_job;
 
 static void *chunk_main(void *arg) {
     chunk_job *c = (chunk_job *)arg;
     /* First pass counts, second pass writes: no reallocation needed. */
     c->count = naive_range(c->t, c->lo, c->hi, c->p, c->m, NULL, 0);
+    if (!c->want_hits) return NULL;
     c->alloc = c->count ? c->count : 1;
     c->hits = (uint64_t *)malloc(c->alloc * sizeof(uint64_t));
     if (!c->hits) { c->failed = 1; return NULL; }
@@ -130,6 +132,7 @@ uint64_t oracle_naive_mt(const uint8_t *t, uint64_t n, const uint8_t *p, uint64_
     if (!jobs || !tid) { free(jobs); free(tid); return UINT64_MAX; }
     for (int c = 0; c < threads; ++c) {
         jobs[c].t = t; jobs[c].p = p; jobs[c].m = m;
+        jobs[c].want_hits = cap > 0;
         jobs[c].lo = starts * (uint64_t)c / (uint64_t)threads;
         jobs[c].hi = starts * (uint64_t)(c + 1) / (uint64_t)threads;
     }
@@ -146,6 +149,10 @@ uint64_t oracle_naive_mt(const uint8_t *t, uint64_t n, const uint8_t *p, uint64_
     int failed = 0;
     for (int c = 0; c < threads; ++c) {
         failed |= jobs[c].failed;
+        if (!jobs[c].want_hits) {
+            total += jobs[c].count;
+            continue;
+        }
         for (uint64_t k = 0; k < jobs[c].count && !jobs[c].failed; ++k) {
             if (total < cap) out[total] = jobs[c].hits[k];
             total++;

@@ -57,6 +57,7 @@ SIGNATURES = {
     "sm_plan_info": (_st, [_vp, ctypes.POINTER(sm_plan_desc)]),
     "sm_search": (_st, [_vp, _u64, _vp, _u32, _vp, _u64, _vp, _vp]),
     "sm_search_plan": (_st, [_vp, _vp, _u64, _vp, _u64, _vp, _vp]),
+    "sm_search_noalloc": (_st, [_vp, _u64, _vp, _u32, _vp, _u64, _vp, _vp]),
     "sm_search_batch": (_st, [ctypes.POINTER(sm_query), _u32, _vp]),
     "sm_batch_create": (_st, [ctypes.POINTER(sm_query), _u32, _u32, _vp, ctypes.POINTER(_vp)]),
     "sm_batch_launch": (_st, [_vp, _vp]),

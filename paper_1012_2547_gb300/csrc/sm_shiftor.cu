@@ -418,3 +418,164 @@ uint64_t so_tile_starts() { return SO_T; }
 uint32_t so_hit_buffer() { return SO_HITS; }
 
 }  // namespace smgpu
+
+// ---------------------------------------------------------------- no-allocation search
+//
+// sm_search_noalloc runs the bit-parallel kernel above without any device
+// allocation: the plan (header + Shift-And masks) and the kernel's scratch
+// (claim counter and one look-back word per work item) live in the
+// file-scope array below, which every GPU that loads this library keeps
+// until the process exits.  Host code must not use the array's name as a
+// device address; it takes the address from cudaGetSymbolAddress once per
+// device (the first call on a device does that set-up, so make that first
+// call before any stream capture).  All calls share the array and it keeps
+// the previous call's contents: the claim counter and the look-back words
+// are cleared on the stream before every launch, and calls whose GPU work
+// overlaps (e.g. on two streams at once) race on it.
+
+#include <mutex>
+
+#include "smgpu.h"
+
+namespace {
+
+constexpr uint32_t NA_MAX_ITEMS = 65536;                 // look-back words
+constexpr size_t NA_CTRL = 256;                          // claim counter, error word
+constexpr size_t NA_PLAN = 4096;                         // plan blob
+constexpr size_t NA_BYTES = NA_CTRL + NA_PLAN + size_t(NA_MAX_ITEMS) * 8;
+constexpr int NA_MAX_DEVICES = 64;
+// Longest text: o + n <= NA_MAX_ITEMS * 64 * SO_T for any o = text & 15, so
+// at most NA_MAX_ITEMS work items of at most 64 sub-tiles are ever needed.
+constexpr uint64_t NA_MAX_N = uint64_t(NA_MAX_ITEMS) * 64 * smgpu::SO_T - 16;
+
+static __device__ __align__(256) uint8_t g_noalloc_scratch[NA_BYTES];
+
+struct NoAllocDevice {
+    bool ready = false;
+    uint8_t *scratch = nullptr;  // device address of g_noalloc_scratch
+    int sms = 0;
+    int bps[4] = {1, 1, 1, 1};   // resident blocks per SM of the four kernels
+};
+
+std::mutex g_noalloc_mu;
+NoAllocDevice g_noalloc_dev[NA_MAX_DEVICES];
+
+const void *na_kernel(int kid) { return smgpu::so_kernel_fn(kid); }
+
+sm_status na_setup(NoAllocDevice **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SM_ECUDA;
+    if (dev < 0 || dev >= NA_MAX_DEVICES) return SM_EINVAL;
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    NoAllocDevice &d = g_noalloc_dev[dev];
+    if (!d.ready) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SM_ECUDA;
+        if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return SM_ECUDA;
+        for (int k = 0; k < 4; ++k) {
+            const size_t smem = smgpu::so_kernel_smem(k);
+            if (cudaFuncSetAttribute(na_kernel(k), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(smem)) != cudaSuccess)
+                return SM_ECUDA;
+            int bps = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, na_kernel(k), 32, smem) !=
+                cudaSuccess)
+                return SM_ECUDA;
+            d.bps[k] = bps > 0 ? bps : 1;
+        }
+        d.scratch = static_cast<uint8_t *>(p);
+        d.ready = true;
+    }
+    *out = &d;
+    return SM_OK;
+}
+
+}  // namespace
+
+extern "C" sm_status sm_search_noalloc(const uint8_t *text, uint64_t n, const uint8_t *pattern,
+                                       uint32_t m, uint64_t *out_pos, uint64_t cap,
+                                       uint64_t *out_count, sm_stream_t stream) {
+    using namespace smgpu;
+    if (!pattern || m == 0 || m > 64) return SM_EINVAL;
+    if (!out_count || (reinterpret_cast<uintptr_t>(out_count) & 7u)) return SM_EINVAL;
+    if (cap > 0 && (!out_pos || (reinterpret_cast<uintptr_t>(out_pos) & 7u))) return SM_EINVAL;
+    if (n > 0 && !text) return SM_EINVAL;
+    if (n > NA_MAX_N) return SM_EINVAL;  // checked before any CUDA call
+    NoAllocDevice *d = nullptr;
+    sm_status st = na_setup(&d);
+    if (st != SM_OK) return st;
+    cudaStream_t s = stream;
+    if (n < m) return cudaMemsetAsync(out_count, 0, sizeof(uint64_t), s) == cudaSuccess ? SM_OK : SM_ECUDA;
+
+    // Work split exactly as sm_search does for this kernel.
+    const int kid = m <= 17 ? K_SO32H : m <= 32 ? K_SO32A : m <= 49 ? K_SO64H : K_SO64A;
+    const uint64_t o = reinterpret_cast<uintptr_t>(text) & 15u;
+    const uint64_t units = (o + n + SO_T - 1) / SO_T;
+    const uint64_t resident = static_cast<uint64_t>(d->sms) * static_cast<uint64_t>(d->bps[kid]);
+    uint64_t per = units / (4 * resident);
+    per = per < 1 ? 1 : (per > 64 ? 64 : per);
+    const uint64_t items = (units + per - 1) / per;
+    if (items > NA_MAX_ITEMS) return SM_EINVAL;  // cannot happen when n <= NA_MAX_N
+
+    // Plan blob on the stack: header, then the 256 Shift-And masks (bit j
+    // of B[c] is 1 iff p[j] = c; bits >= m set so older match flags survive).
+    alignas(16) uint8_t blob[sizeof(PlanDev) + 256 * 8];
+    PlanDev h{};
+    h.m = m;
+    h.variant = VAR_SHIFTOR;
+    h.word_bits = (kid == K_SO32H || kid == K_SO32A) ? 32 : 64;
+    h.hist = (kid == K_SO32H || kid == K_SO64H) ? 1 : 0;
+    h.off_tbl = sizeof(PlanDev);
+    h.tile_starts = SO_T;
+    const uint32_t wbytes = h.word_bits / 8;
+    h.bytes = static_cast<uint32_t>(sizeof(PlanDev) + 256 * wbytes);
+    const uint64_t low = m >= 64 ? ~0ull : ((1ull << m) - 1);
+    for (int c = 0; c < 256; ++c) {
+        uint64_t w = ~low;
+        for (uint32_t j = 0; j < m; ++j)
+            if (pattern[j] == c) w |= 1ull << j;
+        if (wbytes == 4) {
+            const uint32_t w32 = static_cast<uint32_t>(w);
+            memcpy(blob + sizeof(PlanDev) + 4 * c, &w32, 4);
+        } else {
+            memcpy(blob + sizeof(PlanDev) + 8 * c, &w, 8);
+        }
+    }
+    memcpy(blob, &h, sizeof(h));
+
+    uint8_t *ctrl = d->scratch;
+    uint8_t *plan = d->scratch + NA_CTRL;
+    uint64_t *state = reinterpret_cast<uint64_t *>(d->scratch + NA_CTRL + NA_PLAN);
+    // The blob is staged from host memory before the copy call returns.
+    if (cudaMemcpyAsync(plan, blob, h.bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return SM_ECUDA;
+    if (cudaMemsetAsync(ctrl, 0, NA_CTRL, s) != cudaSuccess) return SM_ECUDA;
+    if (cudaMemsetAsync(state, 0, items * sizeof(uint64_t), s) != cudaSuccess) return SM_ECUDA;
+    // All-ones until the last work item writes the true total: a count of
+    // UINT64_MAX after the stream completes means a bounded wait ran out.
+    if (cudaMemsetAsync(out_count, 0xFF, sizeof(uint64_t), s) != cudaSuccess) return SM_ECUDA;
+
+    LaunchArgs a{};
+    a.nq = 1;
+    a.one.text = text;
+    a.one.n = n;
+    a.one.plan = reinterpret_cast<const PlanDev *>(plan);
+    a.one.out_pos = out_pos;
+    a.one.cap = cap;
+    a.one.out_count = out_count;
+    a.one.state = state;
+    a.one.ntiles = items;
+    a.one.first_ticket = 0;
+    a.one.nsub = units;
+    a.one.sub_per_item = static_cast<uint32_t>(per);
+    a.ticket = reinterpret_cast<unsigned long long *>(ctrl);
+    a.total = items;
+    a.err = reinterpret_cast<uint32_t *>(ctrl + 8);
+    const uint64_t full = resident;
+    const int grid = static_cast<int>(items < full ? items : full);
+    void *args[] = {&a};
+    if (cudaLaunchKernel(na_kernel(kid), dim3(grid), dim3(32), args, so_kernel_smem(kid), s) !=
+        cudaSuccess)
+        return SM_ECUDA;
+    return SM_OK;
+}

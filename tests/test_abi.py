@@ -71,6 +71,22 @@ def test_host_argument_checks(lib):
     assert lib.sm_batch_free(None) == _lib.SM_OK
 
 
+def test_noalloc_host_checks(lib):
+    """sm_search_noalloc rejects what it cannot serve before any CUDA call
+    (on this CPU-only host any later step would fail with SM_ECUDA)."""
+    f = lib.sm_search_noalloc
+    fake = 1 << 20  # never dereferenced: the argument checks come first
+    assert f(fake, 1000, bytes(65), 65, fake, 8, fake, None) == _lib.SM_EINVAL
+    assert f(fake, 1000, b"", 0, fake, 8, fake, None) == _lib.SM_EINVAL
+    assert f(None, 1000, b"ab", 2, fake, 8, fake, None) == _lib.SM_EINVAL
+    assert f(fake, 1000, b"ab", 2, fake, 8, fake + 4, None) == _lib.SM_EINVAL
+    longest = 65536 * 64 * 4608 - 16
+    assert f(fake, longest + 1, b"ab", 2, fake, 8, fake, None) == _lib.SM_EINVAL
+    assert f(fake, 1 << 62, b"ab", 2, fake, 8, fake, None) == _lib.SM_EINVAL
+    # within limits the call proceeds to the device, which this host lacks
+    assert f(fake, longest, b"ab", 2, fake, 8, fake, None) == _lib.SM_ECUDA
+
+
 def test_tuning_table_roundtrip(lib):
     smg.tuning_reset()
     cells = smg.tuning_get()

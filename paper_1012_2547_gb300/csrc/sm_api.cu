@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -28,6 +29,8 @@ size_t so_kernel_smem(int kid);
 int so_kernel_threads();
 uint64_t so_tile_starts();
 uint32_t so_hit_buffer();
+uint32_t so_spill_bytes();
+uint32_t so_max_sub();
 const void *qg_kernel_fn(int kid);
 int qg_kernel_threads();
 }  // namespace smgpu
@@ -62,6 +65,7 @@ struct Lib {
     std::unordered_map<std::string, sm_plan *> cache;
     sm_config tuning[SM_TUNE_M_BUCKETS * SM_TUNE_S_BUCKETS];
     std::atomic<uint64_t> launches{0};
+    uint32_t item_cap = 64;  // most units per work item (SMGPU_ITEM_UNITS overrides)
 };
 
 Lib &lib() {
@@ -96,6 +100,10 @@ sm_status ensure_init() {
     SM_TRY_CUDA(cudaMemset(L.err, 0, 256));
     L.device = dev;
     L.sms = sms;
+    if (const char *e = std::getenv("SMGPU_ITEM_UNITS")) {
+        const long v = std::strtol(e, nullptr, 10);
+        if (v >= 1 && v <= 4096) L.item_cap = static_cast<uint32_t>(v);
+    }
     L.inited = true;
     return SM_OK;
 }
@@ -387,8 +395,17 @@ uint32_t sub_per_item(int kid, uint64_t units) {
     const KernelShape &s = lib().shapes[kid];
     const uint64_t resident = static_cast<uint64_t>(lib().sms) * std::max(1, s.blocks_per_sm);
     const uint64_t per = units / (4 * resident);
-    const uint64_t cap = 64;
+    const uint64_t cap = kid <= K_SO64A ? std::min<uint64_t>(lib().item_cap, so_max_sub())
+                                        : lib().item_cap;
     return static_cast<uint32_t>(std::max<uint64_t>(1, std::min<uint64_t>(cap, per)));
+}
+
+// Units per item for one query given the launch's target `per`: the same
+// number of items, but of (nearly) equal size, so that no query ends with a
+// short item whose look-back waits for its longer predecessors.
+uint32_t balanced_per(uint64_t units, uint32_t per) {
+    const uint64_t items = (units + per - 1) / per;
+    return static_cast<uint32_t>((units + items - 1) / items);
 }
 
 bool query_ok(const uint8_t *text, uint64_t n, const sm_plan *plan, const uint64_t *out_pos,
@@ -472,13 +489,15 @@ sm_status search_plan_impl(const sm_plan *plan, const uint8_t *text, uint64_t n,
         SM_TRY_CUDA(cudaMemsetAsync(out_count, 0, sizeof(uint64_t), stream));
         return SM_OK;
     }
-    const uint32_t per = sub_per_item(plan->kid, units);
+    const uint32_t per = balanced_per(units, sub_per_item(plan->kid, units));
     const uint64_t ntiles = (units + per - 1) / per;
-    const size_t bytes = kTicketBytes + ntiles * sizeof(uint64_t);
+    const int grid = grid_for(plan->kid, ntiles);
+    const size_t reset = align16(kTicketBytes + ntiles * sizeof(uint64_t));
+    const size_t spill = plan->kid <= K_SO64A ? static_cast<size_t>(grid) * so_spill_bytes() : 0;
     uint8_t *ws = nullptr;
-    st = get_workspace(stream, bytes, &ws);
+    st = get_workspace(stream, reset + spill, &ws);
     if (st != SM_OK) return st;
-    SM_TRY_CUDA(cudaMemsetAsync(ws, 0, bytes, stream));
+    SM_TRY_CUDA(cudaMemsetAsync(ws, 0, reset, stream));
     LaunchArgs a{};
     a.nq = 1;
     a.one.text = text;
@@ -495,7 +514,8 @@ sm_status search_plan_impl(const sm_plan *plan, const uint8_t *text, uint64_t n,
     a.ticket = reinterpret_cast<unsigned long long *>(ws);
     a.total = ntiles;
     a.err = lib().err;
-    SM_TRY_CUDA(kernel_launch(plan->kid, a, grid_for(plan->kid, ntiles), stream));
+    a.spill = spill ? ws + reset : nullptr;
+    SM_TRY_CUDA(kernel_launch(plan->kid, a, grid, stream));
     return SM_OK;
 }
 
@@ -523,9 +543,11 @@ sm_status batch_build(const sm_query *qs, uint32_t nq, sm_batch *b) {
     }
     uint32_t group_per[K_COUNT];
     for (int k = 0; k < K_COUNT; ++k) group_per[k] = sub_per_item(k, group_units[k]);
+    std::vector<uint32_t> per_q(nq, 1);
     for (uint32_t i = 0; i < nq; ++i) {
-        const uint32_t per = group_per[qs[i].plan->kid];
-        ntiles[i] = (units[i] + per - 1) / per;
+        if (units[i] == 0) continue;
+        per_q[i] = balanced_per(units[i], group_per[qs[i].plan->kid]);
+        ntiles[i] = (units[i] + per_q[i] - 1) / per_q[i];
     }
     uint64_t total_states = 0;
     size_t ndesc = 0;
@@ -537,7 +559,15 @@ sm_status batch_build(const sm_query *qs, uint32_t nq, sm_batch *b) {
     const size_t states_off = kTicketBytes;
     const size_t desc_off = align16(states_off + total_states * sizeof(uint64_t));
     const size_t zero_off = align16(desc_off + ndesc * sizeof(QueryDev));
-    const size_t bytes = zero_off + zero.size() * sizeof(uint64_t *) + 16;
+    size_t spill_need = 0;  // bit-parallel groups run one after another: share one area
+    for (int k = 0; k <= K_SO64A; ++k) {
+        if (by_kid[k].empty()) continue;
+        uint64_t t = 0;
+        for (uint32_t i : by_kid[k]) t += ntiles[i];
+        spill_need = std::max(spill_need, static_cast<size_t>(grid_for(k, t)) * so_spill_bytes());
+    }
+    const size_t spill_off = (zero_off + zero.size() * sizeof(uint64_t *) + 255) & ~size_t(255);
+    const size_t bytes = spill_off + spill_need + 16;
     auto arena = std::make_shared<DevArena>();
     SM_TRY_CUDA(cudaMalloc(&arena->ptr, bytes));
     uint8_t *base = static_cast<uint8_t *>(arena->ptr);
@@ -561,7 +591,7 @@ sm_status batch_build(const sm_query *qs, uint32_t nq, sm_batch *b) {
             d.ntiles = ntiles[i];
             d.first_ticket = ticket;
             d.nsub = units[i];
-            d.sub_per_item = group_per[k];
+            d.sub_per_item = per_q[i];
             ticket += ntiles[i];
             state_pos += ntiles[i];
             desc.push_back(d);
@@ -575,6 +605,7 @@ sm_status batch_build(const sm_query *qs, uint32_t nq, sm_batch *b) {
         g.args.ticket = reinterpret_cast<unsigned long long *>(base) + gi;
         g.args.total = ticket;
         g.args.err = lib().err;
+        g.args.spill = k <= K_SO64A ? base + spill_off : nullptr;
         g.grid = grid_for(k, ticket);
         b->groups.push_back(g);
         ++gi;

@@ -66,6 +66,7 @@ struct LaunchArgs {
     unsigned long long *ticket;  // claim counter, zero at launch
     unsigned long long total;    // total tickets
     uint32_t *err;               // device error word (bit flags)
+    uint8_t *spill;              // bit-parallel kernel: per-block flag spill area, or null
 };
 
 enum : uint32_t { ERR_TIMEOUT = 1u, ERR_COPY = 2u };

@@ -45,6 +45,9 @@ constexpr uint32_t SO_T = 32 * SO_S;        // end positions per sub-tile (one w
 constexpr uint32_t SO_LHALO = 64;           // bytes staged before the sub-tile (>= m-1)
 constexpr uint32_t SO_BUF = SO_LHALO + SO_T;
 constexpr int SO_HITS = 512;                // hits of one work item kept in shared memory
+constexpr uint32_t SO_MAX_SUB = 64;         // most sub-tiles per work item
+constexpr uint32_t SO_SUB_FLAGS = SO_SEGC * 32 * 2;            // 16-bit flags of a sub-tile
+constexpr uint32_t SO_SPILL_BYTES = SO_MAX_SUB * SO_SUB_FLAGS;  // per block
 
 template <typename Word>
 struct SOLayout {
@@ -220,6 +223,7 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
     uint32_t *hits = reinterpret_cast<uint32_t *>(smem + L::HITS_OFF);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L::BAR_OFF);
     const int lane = threadIdx.x;
+    uint8_t *spill = a.spill ? a.spill + static_cast<size_t>(blockIdx.x) * SO_SPILL_BYTES : nullptr;
 
     unsigned long long t = 0;
     uint32_t qi = 0;
@@ -267,20 +271,17 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
         uint32_t count = 0;
         Word carry = 0;
         bool failed = false;
+        bool pending = false;      // a prefetch is in flight when the loop stops early
+        bool spilling = false;     // later sub-tiles' flags go to the spill area
+        uint64_t spill_from = se;  // first spilled sub-tile
+        uint32_t buffered = 0;     // hits in the shared buffer when spilling began
         for (uint64_t s = sb; s < se; ++s) {
-            if (lane == 0) {
-                uint8_t *nb = smem + (cur ^ 1) * SO_BUF;
-                if (s + 1 < se) {
-                    so_issue(nb, &bar[cur ^ 1], Q, s + 1);
-                } else if (so_claim(a, &nt, &nqi, &nk)) {
-                    const QueryDev &Qn = query_of(a, nqi);
-                    so_issue(nb, &bar[cur ^ 1], Qn, nk * Qn.sub_per_item);
-                }
-            }
+            if (lane == 0 && s + 1 < se) so_issue(smem + (cur ^ 1) * SO_BUF, &bar[cur ^ 1], Q, s + 1);
             const bool arrived = mbar_wait_bounded(&bar[cur], (parity >> cur) & 1u);
             parity ^= 1u << cur;
             if (!__all_sync(0xffffffffu, arrived)) {
                 failed = true;
+                pending = s + 1 < se;
                 break;
             }
             const uint8_t *buf = smem + cur * SO_BUF + SO_LHALO;
@@ -298,7 +299,17 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
             const uint32_t cnt = so_mask_count(F, elo, ehi);
             uint32_t total;
             const uint32_t ex = warp_excl_scan(cnt, &total);
-            if (cnt && count + total <= SO_HITS) {
+            if (!spilling && count + total > SO_HITS && spill) {
+                spilling = true;
+                spill_from = s;
+                buffered = count;
+            }
+            if (spilling) {
+                // Keep this sub-tile's flags for the write phase.
+                uint16_t *dst = reinterpret_cast<uint16_t *>(spill + (s - sb) * SO_SUB_FLAGS);
+#pragma unroll
+                for (int c = 0; c < SO_SEGC; ++c) dst[c * 32 + lane] = static_cast<uint16_t>(F[c]);
+            } else if (cnt && count + total <= SO_HITS) {
                 uint32_t idx = count + ex;
                 const uint32_t rel0 = static_cast<uint32_t>(x - ivstart);
 #pragma unroll
@@ -315,33 +326,64 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
             __syncwarp();  // buffer `cur` and the hit buffer are settled
             cur ^= 1;
         }
-        nt = __shfl_sync(0xffffffffu, nt, 0);
-        nqi = __shfl_sync(0xffffffffu, nqi, 0);
-        nk = __shfl_sync(0xffffffffu, nk, 0);
         if (failed) {
+            // The copy of sub-tile `cur` never completed; if a prefetch of
+            // the next sub-tile is in flight, wait (bounded) for it.
             if (lane == 0) {
                 atomicOr(a.err, ERR_COPY);
                 st_relaxed(&Q.state[k], LB_ERR);
-                if (nt < a.total) {
-                    const QueryDev &Qn = query_of(a, nqi);
-                    st_relaxed(&Qn.state[nk], LB_ERR);
-                    mbar_wait_bounded(&bar[cur ^ 1], (parity >> (cur ^ 1)) & 1u);
-                }
+                if (pending) mbar_wait_bounded(&bar[cur ^ 1], (parity >> (cur ^ 1)) & 1u);
             }
             return;
         }
 
-        // ---- item prefix (decoupled look-back), then output
+        // ---- item prefix (decoupled look-back)
         bool ok;
         const uint64_t excl = lookback_exclusive(Q.state, k, count, a.err, &ok);
+        // Claim the next item only now: a warp never holds an unstarted item
+        // while it waits, so waits cannot cascade from query to query.  Its
+        // first sub-tile streams in while this item's hits are written.
+        if (lane == 0 && so_claim(a, &nt, &nqi, &nk)) {
+            const QueryDev &Qn = query_of(a, nqi);
+            so_issue(smem + cur * SO_BUF, &bar[cur], Qn, nk * Qn.sub_per_item);
+        }
+        nt = __shfl_sync(0xffffffffu, nt, 0);
+        nqi = __shfl_sync(0xffffffffu, nqi, 0);
+        nk = __shfl_sync(0xffffffffu, nk, 0);
         if (ok && lane == 0 && k + 1 == Q.ntiles) *Q.out_count = excl + count;
         const uint64_t cap = Q.cap;
         uint64_t *out = Q.out_pos;
         const int64_t shift = static_cast<int64_t>(m) - 1 + o;  // end -> real start
-        if (ok && count <= SO_HITS) {
-            for (uint32_t r = lane; r < count; r += 32) {
+        if (ok && (count <= SO_HITS || spilling)) {
+            const uint32_t nb = spilling ? buffered : count;
+            for (uint32_t r = lane; r < nb; r += 32) {
                 const uint64_t idx = excl + r;
                 if (idx < cap) out[idx] = static_cast<uint64_t>(ivstart + hits[r] - shift);
+            }
+            uint64_t run = excl + nb;
+            for (uint64_t s = spill_from; s < se && run < cap; ++s) {
+                const uint16_t *src = reinterpret_cast<const uint16_t *>(spill + (s - sb) * SO_SUB_FLAGS);
+                uint32_t F[SO_SEGC];
+                uint32_t cnt = 0;
+#pragma unroll
+                for (int c = 0; c < SO_SEGC; ++c) {
+                    F[c] = src[c * 32 + lane];
+                    cnt += __popc(F[c]);
+                }
+                uint32_t total;
+                uint64_t idx = run + warp_excl_scan(cnt, &total);
+                const int64_t x = static_cast<int64_t>(s) * SO_T + lane * SO_S;
+#pragma unroll
+                for (int c = 0; c < SO_SEGC; ++c) {
+                    uint32_t f = F[c];
+                    while (f) {
+                        const int r = 31 - __clz(f);
+                        f ^= 1u << r;
+                        if (idx < cap) out[idx] = static_cast<uint64_t>(x + 16 * c + 15 - r - shift);
+                        ++idx;
+                    }
+                }
+                run += total;
             }
         } else if (ok && excl < cap) {
             // Too many hits to buffer: rescan the item in the free buffer and
@@ -416,6 +458,10 @@ int so_kernel_threads() { return 32; }
 uint64_t so_tile_starts() { return SO_T; }
 
 uint32_t so_hit_buffer() { return SO_HITS; }
+
+uint32_t so_spill_bytes() { return SO_SPILL_BYTES; }
+
+uint32_t so_max_sub() { return SO_MAX_SUB; }
 
 }  // namespace smgpu
 

@@ -200,6 +200,16 @@ def cpu_sample_time(texts, queries, budget_s: float, threads: int):
 
 # ---------------------------------------------------------------- our arm
 
+def sweep_kwargs(args) -> dict:
+    """Subset of the sweep for profiling small cases (--ms, --per-m)."""
+    kw = {}
+    if args.ms:
+        kw["ms"] = tuple(int(x) for x in args.ms.split(","))
+    if args.per_m:
+        kw["per_m"] = args.per_m
+    return kw
+
+
 def family_key(plan) -> tuple:
     i = plan.info()
     return (i.variant, i.word_bits, i.hist)
@@ -227,7 +237,7 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.current_stream()
 
     if args.workload == "sweep":
-        w = workloads.sweep()
+        w = workloads.sweep(**sweep_kwargs(args))
     elif args.workload == "single":
         w = workloads.single()
     else:
@@ -467,7 +477,7 @@ def bench_bandwidth(args, world, rank, local):
 def run_reference(args, world, rank):
     """The reference arm of this tier: the CPU oracle on the host cores."""
     from paper_1012_2547_gb300 import workloads
-    w = workloads.sweep() if args.workload == "sweep" else workloads.single()
+    w = workloads.sweep(**sweep_kwargs(args)) if args.workload == "sweep" else workloads.single()
     threads = os.cpu_count() or 1
     budget = max(1.0, args.ref_seconds / max(1, args.steps + args.warmup))
     times = []
@@ -508,6 +518,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0)
     ap.add_argument("--bw-bytes", type=int, default=8 << 30)
+    ap.add_argument("--ms", default="", help="sweep subset: comma-separated pattern lengths")
+    ap.add_argument("--per-m", type=int, default=0, help="sweep subset: patterns per (text, m)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -210,16 +210,18 @@ def sweep_kwargs(args) -> dict:
     return kw
 
 
-def family_key(plan) -> tuple:
-    i = plan.info()
-    return (i.variant, i.word_bits, i.hist)
+KERNEL_NAMES = ["so_kernel<u32,u8,H>", "so_kernel<u32,u16,H>", "so_kernel<u32,u32,H>",
+                "so_kernel<u32,u32,A>", "so_kernel<u64,u64,H>", "so_kernel<u64,u64,A>",
+                "qg_kernel<qgram>", "qg_kernel<linear>"]
+
+
+def family_key(plan) -> int:
+    """The library runs one persistent launch per kernel id."""
+    return plan.info().kernel
 
 
 def family_name(key) -> str:
-    v, wb, hist = key
-    if v == "shiftor":
-        return f"so_kernel<u{wb},{'H' if hist else 'A'}>"
-    return {"qgram": "qg_kernel<qgram>", "linear": "qg_kernel<linear>"}.get(v, v)
+    return KERNEL_NAMES[key] if 0 <= key < len(KERNEL_NAMES) else str(key)
 
 
 def run_ours(args, world, rank, local):

@@ -56,6 +56,7 @@ class PlanInfo:
     hist: bool
     tile_starts: int
     device_bytes: int
+    kernel: int
 
 
 class Plan:
@@ -79,7 +80,7 @@ class Plan:
         d = _lib.sm_plan_desc()
         check(_lib.load().sm_plan_info(self.handle, ctypes.byref(d)), "sm_plan_info")
         return PlanInfo(d.m, VARIANT_NAMES.get(d.variant, str(d.variant)), d.q, d.word_bits,
-                        bool(d.hist), d.tile_starts, d.device_bytes)
+                        bool(d.hist), d.tile_starts, d.device_bytes, d.kernel)
 
     def free(self):
         if self._h:

@@ -33,7 +33,8 @@ class sm_config(ctypes.Structure):
 class sm_plan_desc(ctypes.Structure):
     _fields_ = [("m", ctypes.c_uint32), ("variant", ctypes.c_uint32), ("q", ctypes.c_uint32),
                 ("word_bits", ctypes.c_uint32), ("hist", ctypes.c_uint32),
-                ("tile_starts", ctypes.c_uint32), ("device_bytes", ctypes.c_uint64)]
+                ("tile_starts", ctypes.c_uint32), ("device_bytes", ctypes.c_uint64),
+                ("kernel", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class sm_query(ctypes.Structure):

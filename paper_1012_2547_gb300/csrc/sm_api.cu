@@ -199,8 +199,9 @@ sm_status build_blob(const uint8_t *p, uint32_t m, uint32_t sigma, const sm_conf
         wb = src->word_bits ? src->word_bits : (m <= 32 ? 32u : 64u);
         if (!explicit_cfg && m > wb) wb = 64;
         if ((wb != 32 && wb != 64) || m > wb) return SM_EINVAL;
-        h.hist = wb == 32 ? (m <= 17) : (m <= 49);
-        kid = wb == 32 ? (h.hist ? K_SO32H : K_SO32A) : (h.hist ? K_SO64H : K_SO64A);
+        kid = so_kid_for(m, wb);
+        if (kid < 0) return SM_EINVAL;
+        h.hist = so_hist(kid) ? 1u : 0u;
         h.variant = VAR_SHIFTOR;
         h.word_bits = wb;
         h.tile_starts = static_cast<uint32_t>(so_tile_starts());
@@ -252,7 +253,8 @@ sm_status build_blob(const uint8_t *p, uint32_t m, uint32_t sigma, const sm_conf
     // Layout.
     size_t off = sizeof(PlanDev);
     h.off_tbl = static_cast<uint32_t>(off);
-    off += h.variant == VAR_SHIFTOR ? 256 * (wb / 8) : 0;
+    const uint32_t esz = h.variant == VAR_SHIFTOR ? so_entry_bytes(kid) : 0;
+    off += 256 * esz;
     off = align16(off);
     h.off_pat = static_cast<uint32_t>(off);
     off += align16(m) + 16;
@@ -273,18 +275,15 @@ sm_status build_blob(const uint8_t *p, uint32_t m, uint32_t sigma, const sm_conf
     uint8_t *b = blob->data();
     if (h.variant == VAR_SHIFTOR) {
         // Shift-And masks: bit j of B[c] is 1 iff p[j] = c; bits >= m are 1
-        // so that older match flags survive the AND.
+        // so that older match flags survive the AND.  Entries keep the low
+        // esz bytes (the kernel supplies the ones above them); stored
+        // little-endian, as the device reads them.
         const uint64_t low = m >= 64 ? ~0ull : ((1ull << m) - 1);
         for (int c = 0; c < 256; ++c) {
             uint64_t w = ~low;
             for (uint32_t j = 0; j < m; ++j)
                 if (p[j] == c) w |= 1ull << j;
-            if (wb == 32) {
-                const uint32_t w32 = static_cast<uint32_t>(w);
-                std::memcpy(b + h.off_tbl + 4 * c, &w32, 4);
-            } else {
-                std::memcpy(b + h.off_tbl + 8 * c, &w, 8);
-            }
+            std::memcpy(b + h.off_tbl + esz * c, &w, esz);
         }
     }
     std::memcpy(b + h.off_pat, p, m);
@@ -395,7 +394,7 @@ uint32_t sub_per_item(int kid, uint64_t units) {
     const KernelShape &s = lib().shapes[kid];
     const uint64_t resident = static_cast<uint64_t>(lib().sms) * std::max(1, s.blocks_per_sm);
     const uint64_t per = units / (4 * resident);
-    const uint64_t cap = kid <= K_SO64A ? std::min<uint64_t>(lib().item_cap, so_max_sub())
+    const uint64_t cap = so_kid(kid) ? std::min<uint64_t>(lib().item_cap, so_max_sub())
                                         : lib().item_cap;
     return static_cast<uint32_t>(std::max<uint64_t>(1, std::min<uint64_t>(cap, per)));
 }
@@ -429,7 +428,7 @@ cudaError_t kernels_init(int sms) {
     (void)sms;
     for (int k = 0; k < K_COUNT; ++k) {
         KernelShape &s = g_shapes[k];
-        if (k <= K_SO64A) {
+        if (so_kid(k)) {
             s.fn = so_kernel_fn(k);
             s.threads = so_kernel_threads();
             s.smem = so_kernel_smem(k);
@@ -452,13 +451,13 @@ cudaError_t kernels_init(int sms) {
 const KernelShape &kernel_shape(int kid) { return g_shapes[kid]; }
 
 uint64_t kernel_tile_starts(int kid, const PlanDev &hdr) {
-    return kid <= K_SO64A ? so_tile_starts() : hdr.tile_starts;
+    return so_kid(kid) ? so_tile_starts() : hdr.tile_starts;
 }
 
 uint64_t kernel_ntiles(int kid, const PlanDev &hdr, const uint8_t *text, uint64_t n) {
     if (n < hdr.m) return 0;
     const uint64_t T = kernel_tile_starts(kid, hdr);
-    if (kid <= K_SO64A) {
+    if (so_kid(kid)) {
         const uint64_t o = reinterpret_cast<uintptr_t>(text) & 15u;
         return (o + n + T - 1) / T;  // staged sub-tiles of end positions
     }
@@ -493,7 +492,7 @@ sm_status search_plan_impl(const sm_plan *plan, const uint8_t *text, uint64_t n,
     const uint64_t ntiles = (units + per - 1) / per;
     const int grid = grid_for(plan->kid, ntiles);
     const size_t reset = align16(kTicketBytes + ntiles * sizeof(uint64_t));
-    const size_t spill = plan->kid <= K_SO64A ? static_cast<size_t>(grid) * so_spill_bytes() : 0;
+    const size_t spill = so_kid(plan->kid) ? static_cast<size_t>(grid) * so_spill_bytes() : 0;
     uint8_t *ws = nullptr;
     st = get_workspace(stream, reset + spill, &ws);
     if (st != SM_OK) return st;
@@ -560,7 +559,7 @@ sm_status batch_build(const sm_query *qs, uint32_t nq, sm_batch *b) {
     const size_t desc_off = align16(states_off + total_states * sizeof(uint64_t));
     const size_t zero_off = align16(desc_off + ndesc * sizeof(QueryDev));
     size_t spill_need = 0;  // bit-parallel groups run one after another: share one area
-    for (int k = 0; k <= K_SO64A; ++k) {
+    for (int k = 0; so_kid(k); ++k) {
         if (by_kid[k].empty()) continue;
         uint64_t t = 0;
         for (uint32_t i : by_kid[k]) t += ntiles[i];
@@ -605,7 +604,7 @@ sm_status batch_build(const sm_query *qs, uint32_t nq, sm_batch *b) {
         g.args.ticket = reinterpret_cast<unsigned long long *>(base) + gi;
         g.args.total = ticket;
         g.args.err = lib().err;
-        g.args.spill = k <= K_SO64A ? base + spill_off : nullptr;
+        g.args.spill = so_kid(k) ? base + spill_off : nullptr;
         g.grid = grid_for(k, ticket);
         b->groups.push_back(g);
         ++gi;
@@ -673,6 +672,7 @@ sm_status sm_plan_info(const sm_plan *plan, sm_plan_desc *out) {
     d.hist = plan->hdr.hist;
     d.tile_starts = static_cast<uint32_t>(kernel_tile_starts(plan->kid, plan->hdr));
     d.device_bytes = plan->hdr.bytes;
+    d.kernel = static_cast<uint32_t>(plan->kid);
     *out = d;
     return SM_OK;
 }

@@ -9,16 +9,35 @@
 
 namespace smgpu {
 
-// Kernel ids.  Every plan maps to exactly one of them.
+// Kernel ids.  Every plan maps to exactly one of them.  The bit-parallel
+// kernels differ in state width (32/64 bits), mask-table entry width (1, 2,
+// 4 or 8 bytes) and how match flags are read ("H": 16 flags kept above bit
+// m-1 of the state; "A": accumulator plus rescan of flagged chunks).
 enum KernelId : int {
-    K_SO32H = 0,  // Shift-And, 32-bit state, 16 match flags kept (m <= 17)
-    K_SO32A = 1,  // Shift-And, 32-bit state, per-chunk accumulator (m <= 32)
-    K_SO64H = 2,  // Shift-And, 64-bit state, 16 match flags kept (m <= 49)
-    K_SO64A = 3,  // Shift-And, 64-bit state, accumulator (m <= 64)
-    K_QGRAM = 4,  // exact q-gram stride filter + warp verification
-    K_LINEAR = 5, // per-segment Knuth-Morris-Pratt
-    K_COUNT = 6
+    K_SO8H = 0,   // 32-bit state, byte masks, m <= 8
+    K_SO16H = 1,  // 32-bit state, half-word masks, m <= 16
+    K_SO32H = 2,  // 32-bit state, word masks, m <= 17
+    K_SO32A = 3,  // 32-bit state, word masks, m <= 32
+    K_SO64H = 4,  // 64-bit state, m <= 49
+    K_SO64A = 5,  // 64-bit state, m <= 64
+    K_QGRAM = 6,  // exact q-gram stride filter + warp verification
+    K_LINEAR = 7, // per-segment Knuth-Morris-Pratt
+    K_COUNT = 8
 };
+
+inline bool so_kid(int kid) { return kid <= K_SO64A; }
+inline uint32_t so_entry_bytes(int kid) {
+    return kid == K_SO8H ? 1u : kid == K_SO16H ? 2u : (kid <= K_SO32A ? 4u : 8u);
+}
+inline uint32_t so_word_bits(int kid) { return kid <= K_SO32A ? 32u : 64u; }
+inline bool so_hist(int kid) { return kid != K_SO32A && kid != K_SO64A; }
+// Bit-parallel kernel for length m and state width wb (0 = choose), or -1.
+inline int so_kid_for(uint32_t m, uint32_t wb) {
+    if (wb == 0) wb = m <= 32 ? 32u : 64u;
+    if (wb == 32) return m <= 8 ? K_SO8H : m <= 16 ? K_SO16H : m <= 17 ? K_SO32H : m <= 32 ? K_SO32A : -1;
+    if (wb == 64) return m <= 49 ? K_SO64H : m <= 64 ? K_SO64A : -1;
+    return -1;
+}
 
 struct KernelShape {
     const void *fn;

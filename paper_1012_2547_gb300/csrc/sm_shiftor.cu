@@ -44,37 +44,93 @@ constexpr int SO_S = SO_SEGC * 16;          // 144 bytes per lane (>= m for m <=
 constexpr uint32_t SO_T = 32 * SO_S;        // end positions per sub-tile (one warp)
 constexpr uint32_t SO_LHALO = 64;           // bytes staged before the sub-tile (>= m-1)
 constexpr uint32_t SO_BUF = SO_LHALO + SO_T;
+constexpr int SO_NBUF = 3;                  // staging ring: two sub-tiles in flight while one is scanned
 constexpr int SO_HITS = 512;                // hits of one work item kept in shared memory
 constexpr uint32_t SO_MAX_SUB = 64;         // most sub-tiles per work item
 constexpr uint32_t SO_SUB_FLAGS = SO_SEGC * 32 * 2;            // 16-bit flags of a sub-tile
 constexpr uint32_t SO_SPILL_BYTES = SO_MAX_SUB * SO_SUB_FLAGS;  // per block
 
-template <typename Word>
+// Dynamic shared memory of a block: the staging ring, the item hit buffer,
+// mbarriers and two run-time constants.  The mask table is a static
+// __shared__ array, so a byte value is directly its (immediate-offset)
+// address.
+template <typename Entry>
 struct SOLayout {
-    static constexpr uint32_t TBL_OFF = 2 * SO_BUF;
-    static constexpr uint32_t HITS_OFF = TBL_OFF + 256 * sizeof(Word);
+    static constexpr uint32_t HITS_OFF = SO_NBUF * SO_BUF;
     static constexpr uint32_t BAR_OFF = HITS_OFF + SO_HITS * 4;
-    static constexpr uint32_t BYTES = BAR_OFF + 16;
+    static constexpr uint32_t CONST_OFF = BAR_OFF + 8 * SO_NBUF;  // multipliers the compiler cannot fold
+    static constexpr uint32_t BYTES = CONST_OFF + 16;
 };
 
-template <typename Word>
-__device__ __forceinline__ void so_step4(Word &D, uint32_t x, const Word *__restrict__ tbl) {
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-        const uint32_t c = __byte_perm(x, 0u, 0x4440u | b);
-        D = ((D << 1) | Word(1)) & tbl[c];
+// Table entry at shared address `addr` (volatile: never merged across a
+// table reload).
+template <typename Entry>
+__device__ __forceinline__ Entry lds_entry(uint32_t addr) {
+    if (sizeof(Entry) == 1) {
+        uint32_t v;
+        asm volatile("ld.shared.u8 %0, [%1];" : "=r"(v) : "r"(addr));
+        return static_cast<Entry>(v);
+    } else if (sizeof(Entry) == 2) {
+        uint16_t v;
+        asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(addr));
+        return static_cast<Entry>(v);
+    } else if (sizeof(Entry) == 4) {
+        uint32_t v;
+        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+        return static_cast<Entry>(v);
+    } else {
+        uint64_t v;
+        asm volatile("ld.shared.u64 %0, [%1];" : "=l"(v) : "r"(addr));
+        return static_cast<Entry>(v);
     }
+}
+
+// Mask of byte b of word x: the table entry widened to the state, with ones
+// above the entry's own bits (so history flags above bit m-1 survive the
+// AND).  `tb` is the table's shared address, 256-aligned: for byte entries
+// one PRMT puts the text byte under tb's upper bytes, which is the entry's
+// address; wider entries take c * esz + tb (esz loaded at run time, so the
+// multiply-add stays on the FMA pipe).
+template <typename Word, typename Entry>
+__device__ __forceinline__ Word so_mask_b(uint32_t x, int b, uint32_t tb, uint32_t esz) {
+    constexpr Word HIGH = sizeof(Entry) < sizeof(Word) ? (~Word(0) << (8 * sizeof(Entry))) : Word(0);
+    uint32_t addr;
+    if (sizeof(Entry) == 1) addr = __byte_perm(x, tb, 0x7650u | b);
+    else addr = __byte_perm(x, 0u, 0x4440u | b) * esz + tb;
+    return Word(lds_entry<Entry>(addr)) | HIGH;
+}
+
+// Mask of byte value c (slow paths).
+template <typename Word, typename Entry>
+__device__ __forceinline__ Word so_mask(uint32_t tb, uint32_t c, uint32_t esz) {
+    constexpr Word HIGH = sizeof(Entry) < sizeof(Word) ? (~Word(0) << (8 * sizeof(Entry))) : Word(0);
+    return Word(lds_entry<Entry>(tb + c * esz)) | HIGH;
+}
+
+// One Shift-And step.  For a 32-bit state, D * two + 1 (two loaded at run
+// time) keeps the shift on the FMA pipe next to the INT ALU's PRMT and AND.
+template <typename Word>
+__device__ __forceinline__ Word so_shift1(Word D, uint32_t two) {
+    if (sizeof(Word) == 4) return static_cast<Word>(static_cast<uint32_t>(D) * two + 1u);
+    return (D << 1) | Word(1);
+}
+
+template <typename Word, typename Entry>
+__device__ __forceinline__ void so_step4(Word &D, uint32_t x, uint32_t tb, uint32_t two,
+                                         uint32_t esz) {
+#pragma unroll
+    for (int b = 0; b < 4; ++b) D = so_shift1(D, two) & so_mask_b<Word, Entry>(x, b, tb, esz);
 }
 
 // Exact flags of one 16-byte chunk (bit 15-b <=> an occurrence ends at byte
 // b of the chunk), re-scanned from the state at the chunk start.
-template <typename Word>
-__device__ __noinline__ uint32_t so_chunk_flags(Word D, const uint8_t *chunk, const Word *tbl,
-                                                uint32_t m) {
+template <typename Word, typename Entry>
+__device__ __noinline__ uint32_t so_chunk_flags(Word D, const uint8_t *chunk, uint32_t tb,
+                                                uint32_t m, uint32_t esz) {
     uint32_t f = 0;
 #pragma unroll 1
     for (int b = 0; b < 16; ++b) {
-        D = ((D << 1) | Word(1)) & tbl[chunk[b]];
+        D = ((D << 1) | Word(1)) & so_mask<Word, Entry>(tb, chunk[b], esz);
         f |= static_cast<uint32_t>((D >> (m - 1)) & Word(1)) << (15 - b);
     }
     return f;
@@ -92,18 +148,17 @@ __device__ __forceinline__ uint32_t range_mask16(int cb, int elo, int ehi) {
 // Local scan of one lane segment from the empty state.  F[c] bit r flags an
 // occurrence ending at segment byte 16c + 15 - r; returns the final state,
 // which is exact because the segment is at least m bytes long.
-template <typename Word, bool HIST>
-__device__ __forceinline__ Word so_local(const uint8_t *seg, const Word *tbl, uint32_t m,
-                                         uint32_t (&F)[SO_SEGC]) {
-    Word D = 0;
+template <typename Word, typename Entry, bool HIST>
+__device__ __forceinline__ Word so_local(const uint8_t *seg, Word D, uint32_t tb, uint32_t m,
+                                         uint32_t two, uint32_t esz, uint32_t (&F)[SO_SEGC]) {
 #pragma unroll
     for (int c = 0; c < SO_SEGC; ++c) {
         const uint4 w = *reinterpret_cast<const uint4 *>(seg + 16 * c);
         if (HIST) {
-            so_step4(D, w.x, tbl);
-            so_step4(D, w.y, tbl);
-            so_step4(D, w.z, tbl);
-            so_step4(D, w.w, tbl);
+            so_step4<Word, Entry>(D, w.x, tb, two, esz);
+            so_step4<Word, Entry>(D, w.y, tb, two, esz);
+            so_step4<Word, Entry>(D, w.z, tb, two, esz);
+            so_step4<Word, Entry>(D, w.w, tb, two, esz);
             F[c] = static_cast<uint32_t>(D >> (m - 1)) & 0xFFFFu;
         } else {
             const Word Ds = D;
@@ -113,13 +168,35 @@ __device__ __forceinline__ Word so_local(const uint8_t *seg, const Word *tbl, ui
                 const uint32_t x = q == 0 ? w.x : q == 1 ? w.y : q == 2 ? w.z : w.w;
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
-                    const uint32_t ch = __byte_perm(x, 0u, 0x4440u | b);
-                    D = ((D << 1) | Word(1)) & tbl[ch];
+                    D = so_shift1(D, two) & so_mask_b<Word, Entry>(x, b, tb, esz);
                     A |= D;
                 }
             }
-            F[c] = ((A >> (m - 1)) & Word(1)) ? so_chunk_flags<Word>(Ds, seg + 16 * c, tbl, m) : 0u;
+            F[c] = ((A >> (m - 1)) & Word(1))
+                       ? so_chunk_flags<Word, Entry>(Ds, seg + 16 * c, tb, m, esz)
+                       : 0u;
         }
+    }
+    return D;
+}
+
+// State at the segment start from the WARM (8 or 16) bytes before it, run
+// from the empty state: exact for every bit below WARM, hence for all bits
+// that matter when m - 1 <= WARM.  Replaces the fix-up for short patterns.
+template <typename Word, typename Entry, int WARM>
+__device__ __forceinline__ Word so_warmup(const uint8_t *seg, uint32_t tb, uint32_t two,
+                                          uint32_t esz) {
+    Word D = 0;
+    if (WARM == 8) {
+        const uint2 w = *reinterpret_cast<const uint2 *>(seg - 8);
+        so_step4<Word, Entry>(D, w.x, tb, two, esz);
+        so_step4<Word, Entry>(D, w.y, tb, two, esz);
+    } else if (WARM == 16) {
+        const uint4 w = *reinterpret_cast<const uint4 *>(seg - 16);
+        so_step4<Word, Entry>(D, w.x, tb, two, esz);
+        so_step4<Word, Entry>(D, w.y, tb, two, esz);
+        so_step4<Word, Entry>(D, w.z, tb, two, esz);
+        so_step4<Word, Entry>(D, w.w, tb, two, esz);
     }
     return D;
 }
@@ -128,15 +205,15 @@ __device__ __forceinline__ Word so_local(const uint8_t *seg, const Word *tbl, ui
 // bytes.  X holds the partial matches inherited from the true state before
 // the segment (bits 0..m-2); they are extended byte by byte until none
 // survives.  Flags are merged into F; returns nothing.
-template <typename Word>
-__device__ __forceinline__ void so_fixup(const uint8_t *seg, const Word *tbl, uint32_t m, Word Dprev,
-                                         uint32_t (&F)[SO_SEGC]) {
+template <typename Word, typename Entry>
+__device__ __forceinline__ void so_fixup(const uint8_t *seg, uint32_t tb, uint32_t m,
+                                         uint32_t esz, Word Dprev, uint32_t (&F)[SO_SEGC]) {
     const Word pm = (Word(1) << (m - 1)) - Word(1);
     Word X = Dprev & pm;
     if (!X) return;
     uint64_t extra = 0;
     for (uint32_t b = 0; X && b + 1 < m; ++b) {
-        X = (X << 1) & tbl[seg[b]];
+        X = (X << 1) & so_mask<Word, Entry>(tb, seg[b], esz);
         extra |= static_cast<uint64_t>((X >> (m - 1)) & Word(1)) << b;
         X &= pm;
     }
@@ -146,26 +223,30 @@ __device__ __forceinline__ void so_fixup(const uint8_t *seg, const Word *tbl, ui
 }
 
 // State after the m-1 bytes that end at `p` (exclusive), from empty.
-template <typename Word>
-__device__ __forceinline__ Word so_warm(const uint8_t *p, const Word *tbl, uint32_t m) {
+template <typename Word, typename Entry>
+__device__ __forceinline__ Word so_warm(const uint8_t *p, uint32_t tb, uint32_t m, uint32_t esz) {
     Word D = 0;
-    for (uint32_t b = 0; b + 1 < m; ++b) D = ((D << 1) | Word(1)) & tbl[p[b]];
+    for (uint32_t b = 0; b + 1 < m; ++b) D = ((D << 1) | Word(1)) & so_mask<Word, Entry>(tb, p[b], esz);
     return D;
 }
 
 // Keep positions e in [elo, ehi) of the segment and count them.
+// (Whole warp.)  Lanes whose segment lies wholly inside the valid range --
+// all of them except at the two ends of a text -- skip the masking.
 __device__ __forceinline__ uint32_t so_mask_count(uint32_t (&F)[SO_SEGC], int elo, int ehi) {
-    uint32_t cnt = 0;
-    if (ehi <= elo) {
-#pragma unroll
-        for (int c = 0; c < SO_SEGC; ++c) F[c] = 0u;
-        return 0;
-    }
     const bool full = elo == 0 && ehi == SO_S;
+    if (!__all_sync(0xffffffffu, full)) {
 #pragma unroll
-    for (int c = 0; c < SO_SEGC; ++c) {
-        if (!full) F[c] &= range_mask16(16 * c, elo, ehi);
-        cnt += __popc(F[c]);
+        for (int c = 0; c < SO_SEGC; ++c)
+            F[c] &= ehi <= elo ? 0u : range_mask16(16 * c, elo, ehi);
+    }
+    uint32_t any = 0;
+#pragma unroll
+    for (int c = 0; c < SO_SEGC; ++c) any |= F[c];
+    uint32_t cnt = 0;
+    if (any) {
+#pragma unroll
+        for (int c = 0; c < SO_SEGC; ++c) cnt += __popc(F[c]);
     }
     return cnt;
 }
@@ -215,11 +296,12 @@ __device__ __forceinline__ bool so_claim(const LaunchArgs &a, unsigned long long
 // from a decoupled look-back, and the buffer is copied out coalesced; an
 // item with more hits than the buffer holds is rescanned and written
 // directly.
-template <typename Word, bool HIST>
+template <typename Word, typename Entry, bool HIST, int WARM>
 __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchArgs a) {
-    using L = SOLayout<Word>;
+    using L = SOLayout<Entry>;
     extern __shared__ __align__(128) uint8_t smem[];
-    Word *tbl = reinterpret_cast<Word *>(smem + L::TBL_OFF);
+    __shared__ __align__(256) uint8_t tbl[256 * sizeof(Entry)];
+    const uint32_t tb = smem_addr(tbl);
     uint32_t *hits = reinterpret_cast<uint32_t *>(smem + L::HITS_OFF);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L::BAR_OFF);
     const int lane = threadIdx.x;
@@ -228,24 +310,30 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
     unsigned long long t = 0;
     uint32_t qi = 0;
     uint64_t k = 0;
+    volatile uint32_t *consts = reinterpret_cast<volatile uint32_t *>(smem + L::CONST_OFF);
     if (lane == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        consts[0] = 2u;
+        consts[1] = static_cast<uint32_t>(sizeof(Entry));
+        for (int b = 0; b < SO_NBUF; ++b) mbar_init(&bar[b], 1);
         fence_mbar_init();
         if (so_claim(a, &t, &qi, &k)) {
             const QueryDev &Q = query_of(a, qi);
-            so_issue(smem, &bar[0], Q, k * Q.sub_per_item);
+            const uint64_t s0 = k * Q.sub_per_item;
+            so_issue(smem, &bar[0], Q, s0);
+            if (s0 + 1 < min(s0 + Q.sub_per_item, Q.nsub)) so_issue(smem + SO_BUF, &bar[1], Q, s0 + 1);
         }
     }
     __syncwarp();
     t = __shfl_sync(0xffffffffu, t, 0);
     qi = __shfl_sync(0xffffffffu, qi, 0);
     k = __shfl_sync(0xffffffffu, k, 0);
+    const uint32_t two = consts[0];
+    const uint32_t esz = consts[1];
 
     const PlanDev *cur_plan = nullptr;
     uint32_t m = 1;
     uint32_t parity = 0;  // bit b: parity of the next phase of bar[b]
-    int cur = 0;          // buffer holding the next sub-tile to scan
+    int cur = 0;          // ring slot holding the next sub-tile to scan
     unsigned long long nt = 0;
     uint32_t nqi = 0;
     uint64_t nk = 0;
@@ -253,9 +341,10 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
         const QueryDev &Q = query_of(a, qi);
         const PlanDev *P = Q.plan;
         if (P != cur_plan) {
-            const Word *src = reinterpret_cast<const Word *>(reinterpret_cast<const uint8_t *>(P) +
-                                                             __ldg(&P->off_tbl));
-            for (int c = lane; c < 256; c += 32) tbl[c] = src[c];
+            const uint4 *src = reinterpret_cast<const uint4 *>(reinterpret_cast<const uint8_t *>(P) +
+                                                               __ldg(&P->off_tbl));
+            for (int c = lane; c < static_cast<int>(256 * sizeof(Entry) / 16); c += 32)
+                reinterpret_cast<uint4 *>(tbl)[c] = __ldg(&src[c]);  // ordered before the scan by __syncwarp
             cur_plan = P;
             m = __ldg(&P->m);
             __syncwarp();
@@ -271,35 +360,41 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
         uint32_t count = 0;
         Word carry = 0;
         bool failed = false;
-        bool pending = false;      // a prefetch is in flight when the loop stops early
+        int pending = 0;           // prefetches in flight when the loop stops early
         bool spilling = false;     // later sub-tiles' flags go to the spill area
         uint64_t spill_from = se;  // first spilled sub-tile
         uint32_t buffered = 0;     // hits in the shared buffer when spilling began
         for (uint64_t s = sb; s < se; ++s) {
-            if (lane == 0 && s + 1 < se) so_issue(smem + (cur ^ 1) * SO_BUF, &bar[cur ^ 1], Q, s + 1);
+            const int ahead = cur == 0 ? SO_NBUF - 1 : cur - 1;  // (cur + 2) mod 3
+            if (lane == 0 && s + 2 < se) so_issue(smem + ahead * SO_BUF, &bar[ahead], Q, s + 2);
             const bool arrived = mbar_wait_bounded(&bar[cur], (parity >> cur) & 1u);
             parity ^= 1u << cur;
             if (!__all_sync(0xffffffffu, arrived)) {
                 failed = true;
-                pending = s + 1 < se;
+                pending = (s + 1 < se) + (s + 2 < se);
                 break;
             }
             const uint8_t *buf = smem + cur * SO_BUF + SO_LHALO;
-            if (s == sb && s > 0 && lane == 0) carry = so_warm(buf - (m - 1), tbl, m);
             const uint8_t *seg = buf + lane * SO_S;
             uint32_t F[SO_SEGC];
-            const Word Dend = so_local<Word, HIST>(seg, tbl, m, F);
-            Word Dprev = __shfl_up_sync(0xffffffffu, Dend, 1);
-            if (lane == 0) Dprev = carry;
-            so_fixup(seg, tbl, m, Dprev, F);
-            carry = __shfl_sync(0xffffffffu, Dend, 31);
+            if (WARM) {
+                so_local<Word, Entry, HIST>(seg, so_warmup<Word, Entry, WARM>(seg, tb, two, esz), tb, m,
+                                            two, esz, F);
+            } else {
+                if (s == sb && s > 0 && lane == 0) carry = so_warm<Word, Entry>(buf - (m - 1), tb, m, esz);
+                const Word Dend = so_local<Word, Entry, HIST>(seg, Word(0), tb, m, two, esz, F);
+                Word Dprev = __shfl_up_sync(0xffffffffu, Dend, 1);
+                if (lane == 0) Dprev = carry;
+                so_fixup<Word, Entry>(seg, tb, m, esz, Dprev, F);
+                carry = __shfl_sync(0xffffffffu, Dend, 31);
+            }
             const int64_t x = static_cast<int64_t>(s) * SO_T + lane * SO_S;
             const int elo = static_cast<int>(vlo - x > 0 ? vlo - x : int64_t(0));
             const int ehi = static_cast<int>(vhi - x < SO_S ? vhi - x : int64_t(SO_S));
             const uint32_t cnt = so_mask_count(F, elo, ehi);
-            uint32_t total;
-            const uint32_t ex = warp_excl_scan(cnt, &total);
-            if (!spilling && count + total > SO_HITS && spill) {
+            uint32_t total = 0, ex = 0;
+            if (__any_sync(0xffffffffu, cnt != 0)) ex = warp_excl_scan(cnt, &total);
+            if (total != 0 && !spilling && count + total > SO_HITS && spill) {
                 spilling = true;
                 spill_from = s;
                 buffered = count;
@@ -323,16 +418,19 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
                 }
             }
             count += total;
-            __syncwarp();  // buffer `cur` and the hit buffer are settled
-            cur ^= 1;
+            __syncwarp();  // slot `cur` and the hit buffer are settled
+            cur = cur == SO_NBUF - 1 ? 0 : cur + 1;
         }
         if (failed) {
-            // The copy of sub-tile `cur` never completed; if a prefetch of
-            // the next sub-tile is in flight, wait (bounded) for it.
+            // The copy of sub-tile `cur` never completed; wait (bounded)
+            // for the prefetches still in flight, then leave.
             if (lane == 0) {
                 atomicOr(a.err, ERR_COPY);
                 st_relaxed(&Q.state[k], LB_ERR);
-                if (pending) mbar_wait_bounded(&bar[cur ^ 1], (parity >> (cur ^ 1)) & 1u);
+                for (int i = 1; i <= pending; ++i) {
+                    const int b = (cur + i) % SO_NBUF;
+                    mbar_wait_bounded(&bar[b], (parity >> b) & 1u);
+                }
             }
             return;
         }
@@ -345,7 +443,10 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
         // first sub-tile streams in while this item's hits are written.
         if (lane == 0 && so_claim(a, &nt, &nqi, &nk)) {
             const QueryDev &Qn = query_of(a, nqi);
-            so_issue(smem + cur * SO_BUF, &bar[cur], Qn, nk * Qn.sub_per_item);
+            const uint64_t s0 = nk * Qn.sub_per_item;
+            so_issue(smem + cur * SO_BUF, &bar[cur], Qn, s0);
+            const int c1 = cur == SO_NBUF - 1 ? 0 : cur + 1;
+            if (s0 + 1 < min(s0 + Qn.sub_per_item, Qn.nsub)) so_issue(smem + c1 * SO_BUF, &bar[c1], Qn, s0 + 1);
         }
         nt = __shfl_sync(0xffffffffu, nt, 0);
         nqi = __shfl_sync(0xffffffffu, nqi, 0);
@@ -388,7 +489,7 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
         } else if (ok && excl < cap) {
             // Too many hits to buffer: rescan the item in the free buffer and
             // write each sub-tile's hits at their final offsets.
-            const int wb = cur ^ 1;
+            const int wb = cur == 0 ? SO_NBUF - 1 : cur - 1;  // the slot the next item leaves idle
             uint64_t run = excl;
             carry = 0;
             for (uint64_t s = sb; s < se && run < cap; ++s) {
@@ -400,14 +501,19 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
                     break;
                 }
                 const uint8_t *buf = smem + wb * SO_BUF + SO_LHALO;
-                if (s == sb && s > 0 && lane == 0) carry = so_warm(buf - (m - 1), tbl, m);
                 const uint8_t *seg = buf + lane * SO_S;
                 uint32_t F[SO_SEGC];
-                const Word Dend = so_local<Word, HIST>(seg, tbl, m, F);
-                Word Dprev = __shfl_up_sync(0xffffffffu, Dend, 1);
-                if (lane == 0) Dprev = carry;
-                so_fixup(seg, tbl, m, Dprev, F);
-                carry = __shfl_sync(0xffffffffu, Dend, 31);
+                if (WARM) {
+                    so_local<Word, Entry, HIST>(seg, so_warmup<Word, Entry, WARM>(seg, tb, two, esz), tb,
+                                                m, two, esz, F);
+                } else {
+                    if (s == sb && s > 0 && lane == 0) carry = so_warm<Word, Entry>(buf - (m - 1), tb, m, esz);
+                    const Word Dend = so_local<Word, Entry, HIST>(seg, Word(0), tb, m, two, esz, F);
+                    Word Dprev = __shfl_up_sync(0xffffffffu, Dend, 1);
+                    if (lane == 0) Dprev = carry;
+                    so_fixup<Word, Entry>(seg, tb, m, esz, Dprev, F);
+                    carry = __shfl_sync(0xffffffffu, Dend, 31);
+                }
                 const int64_t x = static_cast<int64_t>(s) * SO_T + lane * SO_S;
                 const int elo = static_cast<int>(vlo - x > 0 ? vlo - x : int64_t(0));
                 const int ehi = static_cast<int>(vhi - x < SO_S ? vhi - x : int64_t(SO_S));
@@ -441,16 +547,23 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
 
 const void *so_kernel_fn(int kid) {
     switch (kid) {
-        case K_SO32H: return reinterpret_cast<const void *>(&so_kernel<uint32_t, true>);
-        case K_SO32A: return reinterpret_cast<const void *>(&so_kernel<uint32_t, false>);
-        case K_SO64H: return reinterpret_cast<const void *>(&so_kernel<uint64_t, true>);
-        case K_SO64A: return reinterpret_cast<const void *>(&so_kernel<uint64_t, false>);
+        case K_SO8H: return reinterpret_cast<const void *>(&so_kernel<uint32_t, uint8_t, true, 8>);
+        case K_SO16H: return reinterpret_cast<const void *>(&so_kernel<uint32_t, uint16_t, true, 16>);
+        case K_SO32H: return reinterpret_cast<const void *>(&so_kernel<uint32_t, uint32_t, true, 16>);
+        case K_SO32A: return reinterpret_cast<const void *>(&so_kernel<uint32_t, uint32_t, false, 0>);
+        case K_SO64H: return reinterpret_cast<const void *>(&so_kernel<uint64_t, uint64_t, true, 0>);
+        case K_SO64A: return reinterpret_cast<const void *>(&so_kernel<uint64_t, uint64_t, false, 0>);
         default: return nullptr;
     }
 }
 
 size_t so_kernel_smem(int kid) {
-    return (kid == K_SO32H || kid == K_SO32A) ? SOLayout<uint32_t>::BYTES : SOLayout<uint64_t>::BYTES;
+    switch (so_entry_bytes(kid)) {
+        case 1: return SOLayout<uint8_t>::BYTES;
+        case 2: return SOLayout<uint16_t>::BYTES;
+        case 4: return SOLayout<uint32_t>::BYTES;
+        default: return SOLayout<uint64_t>::BYTES;
+    }
 }
 
 int so_kernel_threads() { return 32; }
@@ -500,7 +613,7 @@ struct NoAllocDevice {
     bool ready = false;
     uint8_t *scratch = nullptr;  // device address of g_noalloc_scratch
     int sms = 0;
-    int bps[4] = {1, 1, 1, 1};   // resident blocks per SM of the four kernels
+    int bps[6] = {1, 1, 1, 1, 1, 1};  // resident blocks per SM of the six kernels
 };
 
 std::mutex g_noalloc_mu;
@@ -519,7 +632,7 @@ sm_status na_setup(NoAllocDevice **out) {
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SM_ECUDA;
         if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return SM_ECUDA;
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; smgpu::so_kid(k); ++k) {
             const size_t smem = smgpu::so_kernel_smem(k);
             if (cudaFuncSetAttribute(na_kernel(k), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      static_cast<int>(smem)) != cudaSuccess)
@@ -555,7 +668,7 @@ extern "C" sm_status sm_search_noalloc(const uint8_t *text, uint64_t n, const ui
     if (n < m) return cudaMemsetAsync(out_count, 0, sizeof(uint64_t), s) == cudaSuccess ? SM_OK : SM_ECUDA;
 
     // Work split exactly as sm_search does for this kernel.
-    const int kid = m <= 17 ? K_SO32H : m <= 32 ? K_SO32A : m <= 49 ? K_SO64H : K_SO64A;
+    const int kid = so_kid_for(m, 0);
     const uint64_t o = reinterpret_cast<uintptr_t>(text) & 15u;
     const uint64_t units = (o + n + SO_T - 1) / SO_T;
     const uint64_t resident = static_cast<uint64_t>(d->sms) * static_cast<uint64_t>(d->bps[kid]);
@@ -570,23 +683,18 @@ extern "C" sm_status sm_search_noalloc(const uint8_t *text, uint64_t n, const ui
     PlanDev h{};
     h.m = m;
     h.variant = VAR_SHIFTOR;
-    h.word_bits = (kid == K_SO32H || kid == K_SO32A) ? 32 : 64;
-    h.hist = (kid == K_SO32H || kid == K_SO64H) ? 1 : 0;
+    h.word_bits = so_word_bits(kid);
+    h.hist = so_hist(kid) ? 1 : 0;
     h.off_tbl = sizeof(PlanDev);
     h.tile_starts = SO_T;
-    const uint32_t wbytes = h.word_bits / 8;
-    h.bytes = static_cast<uint32_t>(sizeof(PlanDev) + 256 * wbytes);
+    const uint32_t esz = so_entry_bytes(kid);
+    h.bytes = static_cast<uint32_t>(sizeof(PlanDev) + 256 * esz);
     const uint64_t low = m >= 64 ? ~0ull : ((1ull << m) - 1);
     for (int c = 0; c < 256; ++c) {
         uint64_t w = ~low;
         for (uint32_t j = 0; j < m; ++j)
             if (pattern[j] == c) w |= 1ull << j;
-        if (wbytes == 4) {
-            const uint32_t w32 = static_cast<uint32_t>(w);
-            memcpy(blob + sizeof(PlanDev) + 4 * c, &w32, 4);
-        } else {
-            memcpy(blob + sizeof(PlanDev) + 8 * c, &w, 8);
-        }
+        memcpy(blob + sizeof(PlanDev) + esz * c, &w, esz);  // low esz bytes (little-endian)
     }
     memcpy(blob, &h, sizeof(h));
 

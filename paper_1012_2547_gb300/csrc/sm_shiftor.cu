@@ -33,6 +33,8 @@
 //
 // Positions are handled in a "virtual" frame shifted by o = text & 15, so
 // every staged sub-tile starts on a 16-byte boundary in memory.
+#include <type_traits>
+
 #include "sm_internal.h"
 
 namespace smgpu {
@@ -44,7 +46,10 @@ constexpr int SO_S = SO_SEGC * 16;          // 144 bytes per lane (>= m for m <=
 constexpr uint32_t SO_T = 32 * SO_S;        // end positions per sub-tile (one warp)
 constexpr uint32_t SO_LHALO = 64;           // bytes staged before the sub-tile (>= m-1)
 constexpr uint32_t SO_BUF = SO_LHALO + SO_T;
-constexpr int SO_NBUF = 3;                  // staging ring: two sub-tiles in flight while one is scanned
+#ifndef SO_NBUF_SLOTS
+#define SO_NBUF_SLOTS 3
+#endif
+constexpr int SO_NBUF = SO_NBUF_SLOTS;      // staging ring: SO_NBUF-1 sub-tiles in flight while one is scanned
 constexpr int SO_HITS = 512;                // hits of one work item kept in shared memory
 constexpr uint32_t SO_MAX_SUB = 64;         // most sub-tiles per work item
 constexpr uint32_t SO_SUB_FLAGS = SO_SEGC * 32 * 2;            // 16-bit flags of a sub-tile
@@ -62,64 +67,71 @@ struct SOLayout {
     static constexpr uint32_t BYTES = CONST_OFF + 16;
 };
 
-// Table entry at shared address `addr` (volatile: never merged across a
-// table reload).
+// Table entry at shared address `addr`, zero-extended by the load itself
+// (volatile: never merged across a table reload).
 template <typename Entry>
-__device__ __forceinline__ Entry lds_entry(uint32_t addr) {
-    if (sizeof(Entry) == 1) {
+__device__ __forceinline__ typename std::conditional<sizeof(Entry) == 8, uint64_t, uint32_t>::type
+lds_entry(uint32_t addr) {
+    if constexpr (sizeof(Entry) == 1) {
         uint32_t v;
         asm volatile("ld.shared.u8 %0, [%1];" : "=r"(v) : "r"(addr));
-        return static_cast<Entry>(v);
-    } else if (sizeof(Entry) == 2) {
-        uint16_t v;
-        asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(addr));
-        return static_cast<Entry>(v);
-    } else if (sizeof(Entry) == 4) {
+        return v;
+    } else if constexpr (sizeof(Entry) == 2) {
+        uint32_t v;
+        asm volatile("ld.shared.u16 %0, [%1];" : "=r"(v) : "r"(addr));
+        return v;
+    } else if constexpr (sizeof(Entry) == 4) {
         uint32_t v;
         asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
-        return static_cast<Entry>(v);
+        return v;
     } else {
         uint64_t v;
         asm volatile("ld.shared.u64 %0, [%1];" : "=l"(v) : "r"(addr));
-        return static_cast<Entry>(v);
+        return v;
     }
 }
 
-// Mask of byte b of word x: the table entry widened to the state, with ones
-// above the entry's own bits (so history flags above bit m-1 survive the
-// AND).  `tb` is the table's shared address, 256-aligned: for byte entries
-// one PRMT puts the text byte under tb's upper bytes, which is the entry's
-// address; wider entries take c * esz + tb (esz loaded at run time, so the
-// multiply-add stays on the FMA pipe).
+// Table entry of byte b of word x, widened to the state (zero above the
+// entry's own bits).  `tb` is the table's shared address, 256-aligned: for
+// byte entries one PRMT puts the text byte under tb's upper bytes, which is
+// the entry's address; wider entries take c * esz + tb (esz loaded at run
+// time, so the multiply-add stays on the FMA pipe).
 template <typename Word, typename Entry>
-__device__ __forceinline__ Word so_mask_b(uint32_t x, int b, uint32_t tb, uint32_t esz) {
-    constexpr Word HIGH = sizeof(Entry) < sizeof(Word) ? (~Word(0) << (8 * sizeof(Entry))) : Word(0);
+__device__ __forceinline__ Word so_entry_b(uint32_t x, int b, uint32_t tb, uint32_t esz) {
     uint32_t addr;
     if (sizeof(Entry) == 1) addr = __byte_perm(x, tb, 0x7650u | b);
     else addr = __byte_perm(x, 0u, 0x4440u | b) * esz + tb;
-    return Word(lds_entry<Entry>(addr)) | HIGH;
+    return Word(lds_entry<Entry>(addr));
 }
 
-// Mask of byte value c (slow paths).
+// Mask of byte value c (slow paths): entry plus ones above its own bits.
 template <typename Word, typename Entry>
 __device__ __forceinline__ Word so_mask(uint32_t tb, uint32_t c, uint32_t esz) {
     constexpr Word HIGH = sizeof(Entry) < sizeof(Word) ? (~Word(0) << (8 * sizeof(Entry))) : Word(0);
     return Word(lds_entry<Entry>(tb + c * esz)) | HIGH;
 }
 
-// One Shift-And step.  For a 32-bit state, D * two + 1 (two loaded at run
-// time) keeps the shift on the FMA pipe next to the INT ALU's PRMT and AND.
-template <typename Word>
-__device__ __forceinline__ Word so_shift1(Word D, uint32_t two) {
-    if (sizeof(Word) == 4) return static_cast<Word>(static_cast<uint32_t>(D) * two + 1u);
-    return (D << 1) | Word(1);
+// One Shift-And step D <- ((D << 1) | 1) & B[c] as a single 3-input
+// majority: with D2 = D << 1 (bit 0 clear), e the zero-extended entry and
+// K = (ones above the entry's bits) | 1,
+//   maj(D2, e, K) = (D2 & e) | (K & (D2 | e))
+// gives D2 & e on the entry's bits 1.., e on bit 0 (D2 has none) and D2
+// above the entry (e has none there) -- exactly the update with the ones
+// the table leaves out.  For a 32-bit state the shift is D * two (two
+// loaded at run time: an FMA-pipe IMAD next to the ALU's PRMT and LOP3).
+template <typename Word, typename Entry>
+__device__ __forceinline__ Word so_update(Word D, Word e, uint32_t two) {
+    constexpr Word HIGH = sizeof(Entry) < sizeof(Word) ? (~Word(0) << (8 * sizeof(Entry))) : Word(0);
+    constexpr Word K = HIGH | Word(1);
+    const Word D2 = sizeof(Word) == 4 ? static_cast<Word>(static_cast<uint32_t>(D) * two) : (D << 1);
+    return (D2 & e) | (K & (D2 | e));
 }
 
 template <typename Word, typename Entry>
 __device__ __forceinline__ void so_step4(Word &D, uint32_t x, uint32_t tb, uint32_t two,
                                          uint32_t esz) {
 #pragma unroll
-    for (int b = 0; b < 4; ++b) D = so_shift1(D, two) & so_mask_b<Word, Entry>(x, b, tb, esz);
+    for (int b = 0; b < 4; ++b) D = so_update<Word, Entry>(D, so_entry_b<Word, Entry>(x, b, tb, esz), two);
 }
 
 // Exact flags of one 16-byte chunk (bit 15-b <=> an occurrence ends at byte
@@ -168,7 +180,7 @@ __device__ __forceinline__ Word so_local(const uint8_t *seg, Word D, uint32_t tb
                 const uint32_t x = q == 0 ? w.x : q == 1 ? w.y : q == 2 ? w.z : w.w;
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
-                    D = so_shift1(D, two) & so_mask_b<Word, Entry>(x, b, tb, esz);
+                    D = so_update<Word, Entry>(D, so_entry_b<Word, Entry>(x, b, tb, esz), two);
                     A |= D;
                 }
             }
@@ -265,12 +277,13 @@ __device__ __forceinline__ uint32_t warp_excl_scan(uint32_t v, uint32_t *total) 
 
 // Stage sub-tile s (end positions [s*T, (s+1)*T) in the virtual frame) plus
 // the 64 bytes before it into buffer `dst`.  Lane 0 only.
-__device__ __forceinline__ void so_issue(uint8_t *dst, uint64_t *bar, const QueryDev &Q, uint64_t s) {
-    const uint64_t o = reinterpret_cast<uintptr_t>(Q.text) & 15u;
-    const uint8_t *base = Q.text - o;
+__device__ __forceinline__ void so_issue(uint8_t *dst, uint64_t *bar, const uint8_t *text, uint64_t n,
+                                         uint64_t s) {
+    const uint64_t o = reinterpret_cast<uintptr_t>(text) & 15u;
+    const uint8_t *base = text - o;
     const uint64_t a = s * static_cast<uint64_t>(SO_T);
     const uint64_t lo = a >= SO_LHALO ? a - SO_LHALO : 0;
-    const uint64_t vlim = (o + Q.n + 15u) & ~uint64_t(15);
+    const uint64_t vlim = (o + n + 15u) & ~uint64_t(15);
     const uint64_t hi = min(a + SO_T, vlim);
     const uint32_t bytes = static_cast<uint32_t>(hi - lo);
     fence_proxy_async_smem();
@@ -319,8 +332,9 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
         if (so_claim(a, &t, &qi, &k)) {
             const QueryDev &Q = query_of(a, qi);
             const uint64_t s0 = k * Q.sub_per_item;
-            so_issue(smem, &bar[0], Q, s0);
-            if (s0 + 1 < min(s0 + Q.sub_per_item, Q.nsub)) so_issue(smem + SO_BUF, &bar[1], Q, s0 + 1);
+            const uint64_t s1 = min(s0 + Q.sub_per_item, Q.nsub);
+            for (int i = 0; i < SO_NBUF - 1 && s0 + i < s1; ++i)
+                so_issue(smem + i * SO_BUF, &bar[i], Q.text, Q.n, s0 + i);
         }
     }
     __syncwarp();
@@ -349,11 +363,16 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
             m = __ldg(&P->m);
             __syncwarp();
         }
+        // Query fields in registers: the mbarrier waits are compiler
+        // barriers, after which descriptor fields would be reloaded.
+        const uint8_t *const qtext = Q.text;
+        const uint64_t qn = Q.n;
+        const uint64_t qnsub = Q.nsub;
         const uint64_t sb = k * Q.sub_per_item;
-        const uint64_t se = min(sb + Q.sub_per_item, Q.nsub);
-        const int64_t o = static_cast<int64_t>(reinterpret_cast<uintptr_t>(Q.text) & 15u);
+        const uint64_t se = min(sb + Q.sub_per_item, qnsub);
+        const int64_t o = static_cast<int64_t>(reinterpret_cast<uintptr_t>(qtext) & 15u);
         const int64_t vlo = o + static_cast<int64_t>(m) - 1;  // first valid end
-        const int64_t vhi = o + static_cast<int64_t>(Q.n);    // one past the last
+        const int64_t vhi = o + static_cast<int64_t>(qn);     // one past the last
         const int64_t ivstart = static_cast<int64_t>(sb) * SO_T;
 
         // ---- pass over the item's sub-tiles: count and buffer hits
@@ -365,13 +384,15 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
         uint64_t spill_from = se;  // first spilled sub-tile
         uint32_t buffered = 0;     // hits in the shared buffer when spilling began
         for (uint64_t s = sb; s < se; ++s) {
-            const int ahead = cur == 0 ? SO_NBUF - 1 : cur - 1;  // (cur + 2) mod 3
-            if (lane == 0 && s + 2 < se) so_issue(smem + ahead * SO_BUF, &bar[ahead], Q, s + 2);
+            const int ahead = cur == 0 ? SO_NBUF - 1 : cur - 1;  // (cur + SO_NBUF - 1) mod SO_NBUF
+            if (lane == 0 && s + SO_NBUF - 1 < se)
+                so_issue(smem + ahead * SO_BUF, &bar[ahead], qtext, qn, s + SO_NBUF - 1);
             const bool arrived = mbar_wait_bounded(&bar[cur], (parity >> cur) & 1u);
             parity ^= 1u << cur;
             if (!__all_sync(0xffffffffu, arrived)) {
                 failed = true;
-                pending = (s + 1 < se) + (s + 2 < se);
+                pending = 0;
+                for (int i = 1; i < SO_NBUF; ++i) pending += s + i < se;
                 break;
             }
             const uint8_t *buf = smem + cur * SO_BUF + SO_LHALO;
@@ -389,8 +410,10 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
                 carry = __shfl_sync(0xffffffffu, Dend, 31);
             }
             const int64_t x = static_cast<int64_t>(s) * SO_T + lane * SO_S;
-            const int elo = static_cast<int>(vlo - x > 0 ? vlo - x : int64_t(0));
-            const int ehi = static_cast<int>(vhi - x < SO_S ? vhi - x : int64_t(SO_S));
+            // Only a text's first and last sub-tiles hold invalid ends.
+            const bool edge = s == 0 || s + 1 == qnsub;
+            const int elo = edge ? static_cast<int>(vlo - x > 0 ? vlo - x : int64_t(0)) : 0;
+            const int ehi = edge ? static_cast<int>(vhi - x < SO_S ? vhi - x : int64_t(SO_S)) : SO_S;
             const uint32_t cnt = so_mask_count(F, elo, ehi);
             uint32_t total = 0, ex = 0;
             if (__any_sync(0xffffffffu, cnt != 0)) ex = warp_excl_scan(cnt, &total);
@@ -444,9 +467,11 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
         if (lane == 0 && so_claim(a, &nt, &nqi, &nk)) {
             const QueryDev &Qn = query_of(a, nqi);
             const uint64_t s0 = nk * Qn.sub_per_item;
-            so_issue(smem + cur * SO_BUF, &bar[cur], Qn, s0);
-            const int c1 = cur == SO_NBUF - 1 ? 0 : cur + 1;
-            if (s0 + 1 < min(s0 + Qn.sub_per_item, Qn.nsub)) so_issue(smem + c1 * SO_BUF, &bar[c1], Qn, s0 + 1);
+            const uint64_t s1 = min(s0 + Qn.sub_per_item, Qn.nsub);
+            for (int i = 0; i < SO_NBUF - 1 && s0 + i < s1; ++i) {
+                const int c = (cur + i) % SO_NBUF;
+                so_issue(smem + c * SO_BUF, &bar[c], Qn.text, Qn.n, s0 + i);
+            }
         }
         nt = __shfl_sync(0xffffffffu, nt, 0);
         nqi = __shfl_sync(0xffffffffu, nqi, 0);
@@ -493,7 +518,7 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
             uint64_t run = excl;
             carry = 0;
             for (uint64_t s = sb; s < se && run < cap; ++s) {
-                if (lane == 0) so_issue(smem + wb * SO_BUF, &bar[wb], Q, s);
+                if (lane == 0) so_issue(smem + wb * SO_BUF, &bar[wb], qtext, qn, s);
                 const bool arrived = mbar_wait_bounded(&bar[wb], (parity >> wb) & 1u);
                 parity ^= 1u << wb;
                 if (!__all_sync(0xffffffffu, arrived)) {

@@ -238,6 +238,16 @@ def run_ours(args, world, rank, local):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
 
+    tuning = None
+    if not args.no_tune:
+        # The autotuner picks the kernel per (m bucket, sigma bucket) on
+        # this device before anything is timed.
+        from paper_1012_2547_gb300 import tuner
+        tr = tuner.tune(ms=tuple(int(x) for x in args.ms.split(",")) if args.ms else
+                        tuple(__import__("paper_1012_2547_gb300").gen.SWEEP_M))
+        tuning = {"seconds": tr["seconds"],
+                  "choices": {f"s{r['sigma']}m{r['m']}": r["best"] for r in tr["report"]}}
+
     if args.workload == "sweep":
         w = workloads.sweep(**sweep_kwargs(args))
     elif args.workload == "single":
@@ -418,6 +428,7 @@ def run_ours(args, world, rank, local):
         "clocks": clk,
         "gpu_launches": int(launches),
         "parity_sample": {"searches": len(sample), "ok": parity_ok},
+        "tuning": tuning,
     }
 
 
@@ -517,6 +528,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the built-in kernel rule")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0)
     ap.add_argument("--bw-bytes", type=int, default=8 << 30)

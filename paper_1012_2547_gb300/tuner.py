@@ -1,0 +1,152 @@
+"""Autotuner: (m bucket, sigma bucket) -> kernel configuration, measured on
+the device.
+
+Section 3 of the paper finds that no single algorithm is best for every
+pattern length and alphabet size.  The library therefore keeps a table of
+configurations indexed by the bucket of m (floor(log2 m), 0..11) and of
+sigma (0 = unknown, else floor(log2 sigma) clamped to 1..8), used by
+sm_prepare when no explicit configuration is given (include/smgpu.h,
+sm_tuning_*).  This module fills that table by timing every candidate
+configuration (Shift-Or with a 32- or 64-bit state, q-gram filter for
+q in {3, 4, 5, 6, 8}) on a batch of substring patterns of a uniform text of
+each alphabet size, as one graph-captured batch per candidate, and keeping
+the fastest.  The table can be saved to and loaded from JSON.
+"""
+from __future__ import annotations
+
+import json
+import math
+import statistics
+import time
+
+import numpy as np
+
+from . import Batch, _lib, gen, prepare_many, search_batch, sync, tuning_get, tuning_set
+
+M_BUCKETS = _lib.TUNE_M_BUCKETS
+S_BUCKETS = _lib.TUNE_S_BUCKETS
+VARIANT_IDS = {"shiftor": 1, "qgram": 2, "linear": 3}
+
+
+def m_bucket(m: int) -> int:
+    """floor(log2 m), capped at M_BUCKETS - 1 (same rule as the library)."""
+    return min(M_BUCKETS - 1, max(0, int(m).bit_length() - 1))
+
+
+def s_bucket(sigma: int) -> int:
+    """0 for unknown, else floor(log2 sigma) clamped to 1..S_BUCKETS-1."""
+    if sigma <= 0:
+        return 0
+    return max(1, min(S_BUCKETS - 1, int(sigma).bit_length() - 1))
+
+
+def candidates(m: int) -> list[dict]:
+    out = []
+    if m <= 32:
+        out.append({"variant": "shiftor", "word_bits": 32})
+    if m <= 64:
+        out.append({"variant": "shiftor", "word_bits": 64})
+    for q in (3, 4, 5, 6, 8):
+        if q <= m and m - q + 1 >= 2:
+            out.append({"variant": "qgram", "q": q})
+    return out
+
+
+def _time_batch(text, pats, sigma, cfg, reps, flush):
+    import torch
+    plans = prepare_many(pats, sigma_hint=sigma, **cfg)
+    cnt = torch.zeros(len(plans), dtype=torch.int64, device=text.device)
+    search_batch([(text, p, None, cnt[i:i + 1]) for i, p in enumerate(plans)])
+    sync()
+    c = cnt.cpu().numpy()
+    offs = np.concatenate([[0], np.cumsum(c)])
+    out = torch.empty(max(int(c.sum()), 1), dtype=torch.int64, device=text.device)
+    b = Batch([(text, p, out[int(offs[i]):int(offs[i + 1])], cnt[i:i + 1])
+               for i, p in enumerate(plans)])
+    ts = []
+    for r in range(reps + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.launch()
+        e1.record()
+        torch.cuda.synchronize()
+        if r:
+            ts.append(e0.elapsed_time(e1) / 1e3)
+    sync()
+    b.free()
+    for p in plans:
+        p.free()
+    return statistics.median(ts)
+
+
+def tune(sigmas=(2, 4, 8, 16, 32, 64, 128), ms=gen.SWEEP_M, n: int = 4 << 20, per: int = 16,
+         reps: int = 3, seed: int = 101, apply: bool = True, verbose: bool = False) -> dict:
+    """Measure every candidate for each (sigma, m) and return (and by
+    default apply) the tuning table.  Cells not measured keep variant 0
+    (the library's built-in rule)."""
+    import torch
+
+    from . import gen_text
+
+    t0 = time.perf_counter()
+    cells = [{"variant": 0, "q": 0, "word_bits": 0, "tile": 0} for _ in range(M_BUCKETS * S_BUCKETS)]
+    report = []
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for sigma in sigmas:
+        spec = gen.uniform_text(n, sigma, seed + sigma)
+        text = torch.empty(n, dtype=torch.uint8, device="cuda")
+        gen_text(text, 0, spec.key, sigma)
+        sync()
+        host = None
+        for m in ms:
+            offs = gen.pattern_offsets(n, m, per, seed * 7 + m)
+            pats = [bytes(spec.window(o, m)) for o in offs]
+            res = {}
+            for cfg in candidates(m):
+                key = cfg["variant"] + (f"{cfg.get('word_bits')}" if cfg["variant"] == "shiftor"
+                                        else f"q{cfg.get('q')}")
+                res[key] = (_time_batch(text, pats, sigma, cfg, reps, flush), cfg)
+            best_key = min(res, key=lambda k: res[k][0])
+            best_t, best_cfg = res[best_key]
+            idx = m_bucket(m) * S_BUCKETS + s_bucket(sigma)
+            cells[idx] = {"variant": VARIANT_IDS[best_cfg["variant"]], "q": best_cfg.get("q", 0),
+                          "word_bits": best_cfg.get("word_bits", 0), "tile": 0}
+            row = {"sigma": sigma, "m": m, "best": best_key,
+                   "gbs": {k: round(per * n / v[0] / 1e9, 1) for k, v in res.items()}}
+            report.append(row)
+            if verbose:
+                print(json.dumps(row), flush=True)
+        del host
+    if apply:
+        tuning_set(cells)
+    return {"cells": cells, "report": report, "seconds": round(time.perf_counter() - t0, 2),
+            "n": n, "patterns_per_cell": per}
+
+
+def save(result: dict, path: str) -> None:
+    with open(path, "w") as f:
+        json.dump(result, f, indent=1)
+
+
+def load(path: str, apply: bool = True) -> dict:
+    with open(path) as f:
+        result = json.load(f)
+    if len(result["cells"]) != M_BUCKETS * S_BUCKETS:
+        raise ValueError("tuning table has the wrong shape")
+    if apply:
+        tuning_set(result["cells"])
+    return result
+
+
+def current() -> list[dict]:
+    return tuning_get()
+
+
+if __name__ == "__main__":  # python -m paper_1012_2547_gb300.tuner out.json
+    import sys
+    r = tune(verbose=True)
+    if len(sys.argv) > 1:
+        save(r, sys.argv[1])
+    print("tuned in", r["seconds"], "s")

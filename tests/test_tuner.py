@@ -1,0 +1,44 @@
+"""Autotuner: bucket rules (CPU) and tuned searches staying exact (GPU)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1012_2547_gb300 import gen, tuner
+
+
+def test_buckets_match_library_rule():
+    assert [tuner.m_bucket(m) for m in (1, 2, 3, 4, 7, 8, 1024, 2047, 5000)] == [0, 1, 1, 2, 2, 3, 10, 10, 11]
+    assert [tuner.s_bucket(s) for s in (0, 1, 2, 3, 4, 20, 90, 128, 256, 1000)] == [0, 1, 1, 1, 2, 4, 6, 7, 8, 8]
+
+
+def test_candidates_respect_limits():
+    for m in (1, 2, 5, 17, 33, 64, 65, 1024):
+        for c in tuner.candidates(m):
+            if c["variant"] == "shiftor":
+                assert m <= c["word_bits"]
+            else:
+                assert c["q"] <= m
+
+
+@pytest.mark.gpu
+def test_tuned_table_applies_and_stays_exact():
+    import torch
+
+    import paper_1012_2547_gb300 as smg
+    smg.tuning_reset()
+    r = tuner.tune(sigmas=(4, 64), ms=(8, 64, 256), n=1 << 20, per=4, reps=1)
+    cells = smg.tuning_get()
+    assert cells == r["cells"]
+    for row in r["report"]:
+        i = tuner.m_bucket(row["m"]) * tuner.S_BUCKETS + tuner.s_bucket(row["sigma"])
+        assert cells[i]["variant"] in (1, 2)
+    rng = np.random.default_rng(3)
+    for sigma in (4, 64):
+        t = rng.integers(0, sigma, 300_000, dtype=np.uint8)
+        dev = torch.from_numpy(t).cuda()
+        for m in (8, 64, 256):
+            p = gen.substring_patterns(t, m, 1, seed=m)[0]
+            plan = smg.prepare(p, sigma_hint=sigma)
+            got = smg.search(dev, plan).cpu().numpy().astype(np.uint64)
+            assert np.array_equal(got, oracle.kmp(t, p)), (sigma, m, plan.info())
+    smg.tuning_reset()

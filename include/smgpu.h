@@ -206,6 +206,23 @@ typedef struct {
 sm_status sm_search_batch(const sm_query *queries, uint32_t nq, sm_stream_t stream);
 
 /*
+ * Asynchronous batch in caller-provided device memory (for serving loops that
+ * own their memory budget).  sm_batch_workspace_size returns the bytes a
+ * batch of these queries needs (claim counters, one look-back word per work
+ * item, descriptors, spill area); sm_search_batch_async lays the batch out in
+ * `workspace` (device, 256-byte aligned, at least that many bytes), enqueues
+ * the descriptor upload, the workspace reset and one persistent launch per
+ * kernel family on `stream`, and returns.  The workspace, texts, plans and
+ * outputs must stay valid until the stream reaches this point; the call
+ * allocates nothing.  The descriptor upload is from pageable host memory, so
+ * the call may wait for work already enqueued on `stream`.  Too small a
+ * workspace -> SM_EINVAL.
+ */
+sm_status sm_batch_workspace_size(const sm_query *queries, uint32_t nq, size_t *bytes);
+sm_status sm_search_batch_async(const sm_query *queries, uint32_t nq, void *workspace,
+                                size_t workspace_bytes, sm_stream_t stream);
+
+/*
  * Reusable batch: sm_batch_create uploads the query descriptors once and
  * records the whole batch (workspace reset + one persistent launch per
  * kernel family) as a CUDA graph; sm_batch_launch replays it on `stream`.

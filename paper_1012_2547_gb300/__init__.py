@@ -18,6 +18,7 @@ from ._lib import SM_ETRUNC, SmError, VARIANTS, VARIANT_NAMES, check, sm_config,
 
 __all__ = [
     "Plan", "prepare", "prepare_many", "search", "search_into", "search_plan", "search_batch",
+    "batch_workspace_size", "search_batch_async",
     "Batch", "sync", "gen_text", "tuning_get", "tuning_set", "tuning_reset", "kernel_launches",
     "SmError", "SM_ETRUNC", "lib_path",
 ]
@@ -196,6 +197,28 @@ def _queries(items):
         cap = 0 if out_pos is None else out_pos.numel()
         arr[i] = sm_query(_ptr(text), n, plan.handle, _ptr(out_pos), cap, _ptr(out_count))
     return arr
+
+
+def batch_workspace_size(items) -> int:
+    """sm_batch_workspace_size for (text, plan, out_pos, out_count[, n]) tuples."""
+    if not items:
+        return 0
+    arr = _queries(items)
+    out = ctypes.c_size_t()
+    check(_lib.load().sm_batch_workspace_size(arr, len(items), ctypes.byref(out)),
+          "sm_batch_workspace_size")
+    return int(out.value)
+
+
+def search_batch_async(items, workspace, stream=None) -> None:
+    """sm_search_batch_async: enqueue a batch in caller-provided device
+    workspace (a CUDA uint8 tensor of at least batch_workspace_size bytes,
+    256-byte aligned); no allocation, no host sync."""
+    if not items:
+        return
+    arr = _queries(items)
+    check(_lib.load().sm_search_batch_async(arr, len(items), workspace.data_ptr(), workspace.numel(),
+                                            _stream_ptr(stream)), "sm_search_batch_async")
 
 
 def search_batch(items, stream=None) -> None:

@@ -60,6 +60,8 @@ SIGNATURES = {
     "sm_search_plan": (_st, [_vp, _vp, _u64, _vp, _u64, _vp, _vp]),
     "sm_search_noalloc": (_st, [_vp, _u64, _vp, _u32, _vp, _u64, _vp, _vp]),
     "sm_search_batch": (_st, [ctypes.POINTER(sm_query), _u32, _vp]),
+    "sm_batch_workspace_size": (_st, [ctypes.POINTER(sm_query), _u32, ctypes.POINTER(ctypes.c_size_t)]),
+    "sm_search_batch_async": (_st, [ctypes.POINTER(sm_query), _u32, _vp, ctypes.c_size_t, _vp]),
     "sm_batch_create": (_st, [ctypes.POINTER(sm_query), _u32, _u32, _vp, ctypes.POINTER(_vp)]),
     "sm_batch_launch": (_st, [_vp, _vp]),
     "sm_batch_free": (_st, [_vp]),

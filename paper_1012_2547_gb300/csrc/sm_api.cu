@@ -157,7 +157,8 @@ struct sm_plan {
 };
 
 struct sm_batch {
-    std::shared_ptr<DevArena> arena;  // tickets | states | descriptors | zero list
+    std::shared_ptr<DevArena> arena;  // owning allocation (null for caller workspace)
+    uint8_t *base = nullptr;          // tickets | states | descriptors | zero list | spill
     struct Group {
         int kid;
         LaunchArgs args;
@@ -518,10 +519,19 @@ sm_status search_plan_impl(const sm_plan *plan, const uint8_t *text, uint64_t n,
     return SM_OK;
 }
 
-// Builds the device-side structures of a batch inside `arena` (allocated
-// here) and fills `b` (groups, zero list).  Descriptors are copied with a
-// blocking copy.
-sm_status batch_build(const sm_query *qs, uint32_t nq, sm_batch *b) {
+// Host-side layout of a batch's device structures at `base` (may be null
+// when only the size is wanted): claim counters | look-back words |
+// descriptors | zero-count list | flag spill area.  Fills b->groups and the
+// host copies of the descriptor and zero arrays.
+struct BatchLayout {
+    size_t bytes = 0;
+    size_t desc_off = 0;
+    size_t zero_off = 0;
+    std::vector<QueryDev> desc;
+    std::vector<uint64_t *> zero;
+};
+
+sm_status batch_layout(const sm_query *qs, uint32_t nq, uint8_t *base, sm_batch *b, BatchLayout *L) {
     for (uint32_t i = 0; i < nq; ++i)
         if (!query_ok(qs[i].text, qs[i].n, qs[i].plan, qs[i].out_pos, qs[i].cap, qs[i].out_count))
             return SM_EINVAL;
@@ -529,12 +539,14 @@ sm_status batch_build(const sm_query *qs, uint32_t nq, sm_batch *b) {
     if (st != SM_OK) return st;
     // Group by kernel, keeping input order inside a group.
     std::vector<std::vector<uint32_t>> by_kid(K_COUNT);
-    std::vector<uint64_t *> zero;
+    L->zero.clear();
+    L->desc.clear();
+    b->groups.clear();
     std::vector<uint64_t> units(nq), ntiles(nq);
     uint64_t group_units[K_COUNT] = {};
     for (uint32_t i = 0; i < nq; ++i) {
         units[i] = kernel_ntiles(qs[i].plan->kid, qs[i].plan->hdr, qs[i].text, qs[i].n);
-        if (units[i] == 0) zero.push_back(qs[i].out_count);
+        if (units[i] == 0) L->zero.push_back(qs[i].out_count);
         else {
             by_kid[qs[i].plan->kid].push_back(i);
             group_units[qs[i].plan->kid] += units[i];
@@ -556,8 +568,8 @@ sm_status batch_build(const sm_query *qs, uint32_t nq, sm_batch *b) {
             ++ndesc;
         }
     const size_t states_off = kTicketBytes;
-    const size_t desc_off = align16(states_off + total_states * sizeof(uint64_t));
-    const size_t zero_off = align16(desc_off + ndesc * sizeof(QueryDev));
+    L->desc_off = align16(states_off + total_states * sizeof(uint64_t));
+    L->zero_off = align16(L->desc_off + ndesc * sizeof(QueryDev));
     size_t spill_need = 0;  // bit-parallel groups run one after another: share one area
     for (int k = 0; so_kid(k); ++k) {
         if (by_kid[k].empty()) continue;
@@ -565,18 +577,14 @@ sm_status batch_build(const sm_query *qs, uint32_t nq, sm_batch *b) {
         for (uint32_t i : by_kid[k]) t += ntiles[i];
         spill_need = std::max(spill_need, static_cast<size_t>(grid_for(k, t)) * so_spill_bytes());
     }
-    const size_t spill_off = (zero_off + zero.size() * sizeof(uint64_t *) + 255) & ~size_t(255);
-    const size_t bytes = spill_off + spill_need + 16;
-    auto arena = std::make_shared<DevArena>();
-    SM_TRY_CUDA(cudaMalloc(&arena->ptr, bytes));
-    uint8_t *base = static_cast<uint8_t *>(arena->ptr);
-    std::vector<QueryDev> desc;
-    desc.reserve(ndesc);
+    const size_t spill_off = (L->zero_off + L->zero.size() * sizeof(uint64_t *) + 255) & ~size_t(255);
+    L->bytes = spill_off + spill_need + 16;
+    L->desc.reserve(ndesc);
     uint64_t state_pos = 0;
     int gi = 0;
     for (int k = 0; k < K_COUNT; ++k) {
         if (by_kid[k].empty()) continue;
-        const size_t first_desc = desc.size();
+        const size_t first_desc = L->desc.size();
         uint64_t ticket = 0;
         for (uint32_t i : by_kid[k]) {
             QueryDev d{};
@@ -593,14 +601,14 @@ sm_status batch_build(const sm_query *qs, uint32_t nq, sm_batch *b) {
             d.sub_per_item = per_q[i];
             ticket += ntiles[i];
             state_pos += ntiles[i];
-            desc.push_back(d);
+            L->desc.push_back(d);
         }
         if (gi >= static_cast<int>(kTicketBytes / 8)) return SM_EINVAL;
         sm_batch::Group g{};
         g.kid = k;
-        g.args.qs = reinterpret_cast<const QueryDev *>(base + desc_off) + first_desc;
+        g.args.qs = reinterpret_cast<const QueryDev *>(base + L->desc_off) + first_desc;
         g.args.nq = static_cast<uint32_t>(by_kid[k].size());
-        if (g.args.nq == 1) g.args.one = desc[first_desc];
+        if (g.args.nq == 1) g.args.one = L->desc[first_desc];
         g.args.ticket = reinterpret_cast<unsigned long long *>(base) + gi;
         g.args.total = ticket;
         g.args.err = lib().err;
@@ -609,22 +617,37 @@ sm_status batch_build(const sm_query *qs, uint32_t nq, sm_batch *b) {
         b->groups.push_back(g);
         ++gi;
     }
-    if (!desc.empty())
-        SM_TRY_CUDA(cudaMemcpy(base + desc_off, desc.data(), desc.size() * sizeof(QueryDev),
-                               cudaMemcpyHostToDevice));
-    if (!zero.empty())
-        SM_TRY_CUDA(cudaMemcpy(base + zero_off, zero.data(), zero.size() * sizeof(uint64_t *),
-                               cudaMemcpyHostToDevice));
-    b->arena = arena;
-    b->zero_list = reinterpret_cast<uint64_t **>(base + zero_off);
-    b->nzero = static_cast<uint32_t>(zero.size());
-    b->reset_bytes = desc_off;
+    b->base = base;
+    b->zero_list = reinterpret_cast<uint64_t **>(base + L->zero_off);
+    b->nzero = static_cast<uint32_t>(L->zero.size());
+    b->reset_bytes = L->desc_off;
     b->kernels = static_cast<uint32_t>(b->groups.size()) + (b->nzero ? 1u : 0u);
     return SM_OK;
 }
 
+// Builds a batch in its own device allocation (descriptors copied with a
+// blocking copy).
+sm_status batch_build(const sm_query *qs, uint32_t nq, sm_batch *b) {
+    BatchLayout L;
+    sm_status st = batch_layout(qs, nq, nullptr, b, &L);
+    if (st != SM_OK) return st;
+    auto arena = std::make_shared<DevArena>();
+    SM_TRY_CUDA(cudaMalloc(&arena->ptr, L.bytes));
+    uint8_t *base = static_cast<uint8_t *>(arena->ptr);
+    st = batch_layout(qs, nq, base, b, &L);
+    if (st != SM_OK) return st;
+    if (!L.desc.empty())
+        SM_TRY_CUDA(cudaMemcpy(base + L.desc_off, L.desc.data(), L.desc.size() * sizeof(QueryDev),
+                               cudaMemcpyHostToDevice));
+    if (!L.zero.empty())
+        SM_TRY_CUDA(cudaMemcpy(base + L.zero_off, L.zero.data(), L.zero.size() * sizeof(uint64_t *),
+                               cudaMemcpyHostToDevice));
+    b->arena = arena;
+    return SM_OK;
+}
+
 sm_status batch_enqueue(const sm_batch *b, cudaStream_t stream) {
-    SM_TRY_CUDA(cudaMemsetAsync(b->arena->ptr, 0, b->reset_bytes, stream));
+    SM_TRY_CUDA(cudaMemsetAsync(b->base, 0, b->reset_bytes, stream));
     if (b->nzero) SM_TRY_CUDA(launch_zero_counts(b->zero_list, b->nzero, stream));
     for (const auto &g : b->groups) SM_TRY_CUDA(kernel_launch(g.kid, g.args, g.grid, stream));
     return SM_OK;
@@ -724,6 +747,41 @@ sm_status sm_search_batch(const sm_query *queries, uint32_t nq, sm_stream_t stre
     // The batch's device memory must outlive the enqueued work.
     SM_TRY_CUDA(cudaStreamSynchronize(stream));
     return SM_OK;
+}
+
+sm_status sm_batch_workspace_size(const sm_query *queries, uint32_t nq, size_t *bytes) {
+    if (!bytes || (nq > 0 && !queries)) return SM_EINVAL;
+    if (nq == 0) {
+        *bytes = 0;
+        return SM_OK;
+    }
+    sm_batch b;
+    BatchLayout L;
+    sm_status st = batch_layout(queries, nq, nullptr, &b, &L);
+    if (st == SM_OK) *bytes = L.bytes;
+    return st;
+}
+
+sm_status sm_search_batch_async(const sm_query *queries, uint32_t nq, void *workspace,
+                                size_t workspace_bytes, sm_stream_t stream) {
+    if (nq == 0) return SM_OK;
+    if (!queries || !workspace || (reinterpret_cast<uintptr_t>(workspace) & 255u)) return SM_EINVAL;
+    sm_batch b;
+    BatchLayout L;
+    sm_status st = batch_layout(queries, nq, nullptr, &b, &L);
+    if (st != SM_OK) return st;
+    if (L.bytes > workspace_bytes) return SM_EINVAL;
+    uint8_t *base = static_cast<uint8_t *>(workspace);
+    st = batch_layout(queries, nq, base, &b, &L);
+    if (st != SM_OK) return st;
+    // Pageable sources: each copy returns once its bytes are staged.
+    if (!L.desc.empty())
+        SM_TRY_CUDA(cudaMemcpyAsync(base + L.desc_off, L.desc.data(), L.desc.size() * sizeof(QueryDev),
+                                    cudaMemcpyHostToDevice, stream));
+    if (!L.zero.empty())
+        SM_TRY_CUDA(cudaMemcpyAsync(base + L.zero_off, L.zero.data(),
+                                    L.zero.size() * sizeof(uint64_t *), cudaMemcpyHostToDevice, stream));
+    return batch_enqueue(&b, stream);
 }
 
 sm_status sm_batch_create(const sm_query *queries, uint32_t nq, uint32_t flags, sm_stream_t stream,

@@ -1,0 +1,287 @@
+"""Serving loop: continuous batching of exact-match queries on one GPU.
+
+Requests arrive at any time (``Server.submit``); each names a resident
+corpus (a device text loaded once) or carries its own text.  A scheduler
+thread repeatedly
+
+  1. retires finished batches (their stream's event has fired): reads the
+     counts and positions copied back on that stream, completes the
+     requests' futures, re-queues any request whose output was truncated
+     with its exact count as the new capacity, and returns its memory to
+     the budget;
+  2. admits pending requests while their device memory (own text, plan,
+     output capacity, count) plus the batch workspace fits the budget,
+     taking requests of one length class (floor(log2 m): the class of the
+     oldest pending request) in arrival order, up to ``max_batch``;
+  3. launches the batch on a free stream with ``sm_search_batch_async``
+     (one persistent launch per kernel family, in memory the server owns),
+     followed by the device-to-host copies of counts and positions and an
+     event.
+
+Up to ``streams`` batches are in flight at once, so requests that arrive
+while others run are admitted as slots and memory free up and their work
+overlaps on the device.  Every request records arrival and completion times
+(p50 / p99 latency).  ``Policy`` holds the host-side decisions (admission,
+length classes, batch size) and needs no GPU.
+"""
+from __future__ import annotations
+
+import collections
+import concurrent.futures as cf
+import itertools
+import threading
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+def length_class(m: int) -> int:
+    """floor(log2 m) capped at 11 (the tuning table's m bucket)."""
+    return min(11, max(0, int(m).bit_length() - 1))
+
+
+@dataclass
+class Request:
+    rid: int
+    pattern: bytes
+    corpus: str | None
+    text: np.ndarray | None
+    cap: int
+    t_arrival: float
+    future: cf.Future = field(default_factory=cf.Future)
+    attempts: int = 0
+
+    @property
+    def m(self) -> int:
+        return len(self.pattern)
+
+
+def plan_bytes_estimate(m: int) -> int:
+    """Upper bound of a plan's device bytes (header, masks, pattern, q-gram
+    table, border table), for admission only."""
+    return 4096 + 64 * m
+
+
+class Policy:
+    """Host-side scheduling decisions.  No GPU work."""
+
+    def __init__(self, budget_bytes: int, max_batch: int = 512, max_wait: float = 0.0005,
+                 corpus_bytes=None, workspace_per_batch: int = 128 << 20):
+        self.budget = int(budget_bytes)
+        self.max_batch = int(max_batch)
+        self.max_wait = float(max_wait)
+        self.used = 0
+        self.pending: collections.deque[Request] = collections.deque()
+        self.corpus_bytes = dict(corpus_bytes or {})
+        self.workspace_per_batch = int(workspace_per_batch)
+
+    def need(self, r: Request) -> int:
+        own = 0 if r.text is None else len(r.text)
+        return own + plan_bytes_estimate(r.m) + 8 * max(r.cap, 1) + 8
+
+    def push(self, r: Request, front: bool = False) -> None:
+        (self.pending.appendleft if front else self.pending.append)(r)
+
+    def ready(self, now: float, busy: int) -> bool:
+        """Launch now?  A full batch, an old enough request, or an idle GPU."""
+        if not self.pending:
+            return False
+        return (len(self.pending) >= self.max_batch or busy == 0
+                or now - self.pending[0].t_arrival >= self.max_wait)
+
+    def take(self) -> tuple[list[Request], int, list[Request]]:
+        """Pick the next batch: requests of the oldest request's length class,
+        in arrival order, while they fit the budget.  Returns (batch, bytes
+        reserved, requests rejected because they can never fit)."""
+        rejected, batch = [], []
+        while self.pending and self.need(self.pending[0]) + self.workspace_per_batch > self.budget:
+            rejected.append(self.pending.popleft())
+        if not self.pending:
+            return [], 0, rejected
+        cls = length_class(self.pending[0].m)
+        reserved = self.workspace_per_batch
+        if self.used + reserved > self.budget:
+            return [], 0, rejected
+        keep = collections.deque()
+        while self.pending and len(batch) < self.max_batch:
+            r = self.pending.popleft()
+            need = self.need(r)
+            if length_class(r.m) == cls and self.used + reserved + need <= self.budget:
+                batch.append(r)
+                reserved += need
+            else:
+                keep.append(r)
+                if self.used + reserved + need > self.budget and length_class(r.m) == cls:
+                    break  # memory is full: later requests of this class wait too
+        keep.extend(self.pending)
+        self.pending = keep
+        if not batch:
+            return [], 0, rejected
+        self.used += reserved
+        return batch, reserved, rejected
+
+    def release(self, nbytes: int) -> None:
+        self.used -= nbytes
+
+
+class Server:
+    """Continuous-batching exact-match server on one GPU (see module doc)."""
+
+    def __init__(self, corpora: dict, budget_bytes: int = 40 << 30, streams: int = 4,
+                 max_batch: int = 512, max_wait: float = 0.0005, first_cap: int = 256,
+                 sigma_hints: dict | None = None, own_text_sigma: int = 0):
+        import torch
+
+        import paper_1012_2547_gb300 as smg
+        self._torch = torch
+        self._smg = smg
+        self.corpora = dict(corpora)
+        self.sigma_hints = dict(sigma_hints or {})
+        self.own_text_sigma = own_text_sigma
+        self.first_cap = int(first_cap)
+        self.policy = Policy(budget_bytes, max_batch, max_wait,
+                             {k: v.numel() for k, v in self.corpora.items()})
+        self.streams = [torch.cuda.Stream() for _ in range(streams)]
+        self.inflight: list[dict | None] = [None] * streams
+        self.latencies: list[float] = []
+        self.completed = 0
+        self.retries = 0
+        self.batches = 0
+        self._ids = itertools.count()
+        self._lock = threading.Lock()
+        self._wake = threading.Event()
+        self._stop = False
+        self._error: BaseException | None = None
+        self._thread = threading.Thread(target=self._run, name="smgpu-serve", daemon=True)
+        self._thread.start()
+
+    # ---------------------------------------------------------------- API
+
+    def submit(self, pattern, corpus: str | None = None, text=None) -> cf.Future:
+        p = bytes(pattern)
+        if not p:
+            raise ValueError("empty pattern")
+        if (corpus is None) == (text is None):
+            raise ValueError("give exactly one of corpus and text")
+        if corpus is not None and corpus not in self.corpora:
+            raise KeyError(corpus)
+        t = None if text is None else np.ascontiguousarray(np.frombuffer(bytes(text), np.uint8)
+                                                          if isinstance(text, (bytes, bytearray))
+                                                          else text, dtype=np.uint8)
+        n = len(t) if t is not None else self.corpora[corpus].numel()
+        r = Request(next(self._ids), p, corpus, t, min(self.first_cap, max(n - len(p) + 1, 1)),
+                    time.perf_counter())
+        with self._lock:
+            self.policy.push(r)
+        self._wake.set()
+        return r.future
+
+    def close(self, timeout: float | None = None) -> None:
+        self._stop = True
+        self._wake.set()
+        self._thread.join(timeout)
+        if self._error is not None:
+            raise self._error
+
+    def stats(self) -> dict:
+        lat = np.array(self.latencies) if self.latencies else np.zeros(1)
+        return {"completed": self.completed, "batches": self.batches, "retries": self.retries,
+                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3)}
+
+    # ---------------------------------------------------------------- loop
+
+    def _run(self):
+        torch = self._torch
+        try:
+            while True:
+                progressed = self._retire()
+                with self._lock:
+                    busy = sum(x is not None for x in self.inflight)
+                    slot = next((i for i, x in enumerate(self.inflight) if x is None), None)
+                    batch, reserved, rejected = ([], 0, [])
+                    if slot is not None and self.policy.ready(time.perf_counter(), busy):
+                        batch, reserved, rejected = self.policy.take()
+                    idle = not self.policy.pending and busy == 0
+                for r in rejected:
+                    r.future.set_exception(MemoryError("request larger than the device budget"))
+                if batch:
+                    self._launch(slot, batch, reserved)
+                    progressed = True
+                if self._stop and idle and not batch:
+                    break
+                if not progressed:
+                    self._wake.wait(0.0002)
+                    self._wake.clear()
+        except BaseException as e:  # surface errors to close()
+            self._error = e
+            with self._lock:
+                pending = list(self.policy.pending)
+            for r in pending:
+                if not r.future.done():
+                    r.future.set_exception(e)
+        finally:
+            torch.cuda.synchronize()
+
+    def _launch(self, slot: int, batch: list[Request], reserved: int) -> None:
+        torch, smg = self._torch, self._smg
+        s = self.streams[slot]
+        dev = torch.device("cuda")
+        with torch.cuda.stream(s):
+            texts = []
+            for r in batch:
+                if r.text is not None:
+                    texts.append(torch.from_numpy(r.text).to(dev, non_blocking=False))
+                else:
+                    texts.append(self.corpora[r.corpus])
+            hint = self.sigma_hints.get(batch[0].corpus, self.own_text_sigma)
+            plans = smg.prepare_many([r.pattern for r in batch], sigma_hint=hint)
+            caps = np.array([r.cap for r in batch], dtype=np.int64)
+            offs = np.concatenate([[0], np.cumsum(caps)])
+            out = torch.empty(int(offs[-1]) or 1, dtype=torch.int64, device=dev)
+            cnt = torch.empty(len(batch), dtype=torch.int64, device=dev)
+            items = [(texts[i], plans[i], out[int(offs[i]):int(offs[i + 1])], cnt[i:i + 1])
+                     for i in range(len(batch))]
+            ws = torch.empty(max(smg.batch_workspace_size(items), 256), dtype=torch.uint8, device=dev)
+            smg.search_batch_async(items, ws, stream=s)
+            cnt_h = torch.empty(len(batch), dtype=torch.int64, pin_memory=True)
+            out_h = torch.empty(out.numel(), dtype=torch.int64, pin_memory=True)
+            cnt_h.copy_(cnt, non_blocking=True)
+            out_h.copy_(out, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(s)
+        self.inflight[slot] = {"batch": batch, "event": ev, "cnt_h": cnt_h, "out_h": out_h,
+                               "offs": offs, "keep": (texts, plans, out, cnt, ws), "reserved": reserved}
+        self.batches += 1
+
+    def _retire(self) -> bool:
+        done_any = False
+        for i, rec in enumerate(self.inflight):
+            if rec is None or not rec["event"].query():
+                continue
+            done_any = True
+            now = time.perf_counter()
+            counts = rec["cnt_h"].numpy()
+            out_h = rec["out_h"].numpy()
+            offs = rec["offs"]
+            requeue = []
+            for j, r in enumerate(rec["batch"]):
+                c = int(counts[j])
+                if c > r.cap:
+                    r.cap = c
+                    r.attempts += 1
+                    requeue.append(r)
+                    continue
+                pos = out_h[int(offs[j]):int(offs[j]) + c].astype(np.uint64)
+                self.latencies.append(now - r.t_arrival)
+                self.completed += 1
+                r.future.set_result(pos)
+            for p in rec["keep"][1]:
+                p.free()
+            with self._lock:
+                self.policy.release(rec["reserved"])
+                for r in reversed(requeue):
+                    self.policy.push(r, front=True)
+                self.retries += len(requeue)
+                self.inflight[i] = None
+        return done_any

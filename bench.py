@@ -485,6 +485,129 @@ def bench_bandwidth(args, world, rank, local):
     print(json.dumps({"workload": w.name, "peak_gbs": hbm, "peak_kind": kind, "results": res}))
 
 
+# ---------------------------------------------------------------- serving workload
+
+def bench_serve(args, world, rank, local):
+    """Serving (continuous batching) vs one launch per query, on two resident
+    corpora (uniform sigma = 4 and Zipf English-like), m log-uniform in
+    [2, 512], 70 % corpus queries and 30 % carrying their own text
+    (log-uniform 4 KiB .. 16 MiB).  Reports saturated queries/s of both
+    paths and p50/p99 latency under Poisson arrivals at fractions of the
+    batched capacity."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1012_2547_gb300 as smg
+    from paper_1012_2547_gb300 import gen
+    from paper_1012_2547_gb300.serve import Server
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    C = args.serve_corpus
+    specs = {"rand4": gen.uniform_text(C, 4, 61), "english": gen.english_text(C, 62)}
+    hints = {"rand4": 4, "english": 90}
+    corp = {}
+    for k, sp in specs.items():
+        t = torch.empty(C, dtype=torch.uint8, device=dev)
+        if sp.kind == "uniform":
+            smg.gen_text(t, 0, sp.key, sp.sigma)
+        else:
+            thr = torch.tensor(np.asarray(sp.thresholds, dtype=np.uint32).view(np.int32), device=dev)
+            bm = torch.tensor(np.asarray(sp.byte_map, dtype=np.uint8), device=dev)
+            smg.gen_text(t, 0, sp.key, 0, thr, bm)
+        corp[k] = t
+    smg.sync()
+    pool = {4: gen.uniform_text(64 << 20, 4, 63).host(), 90: gen.english_text(64 << 20, 64).host()}
+    key = gen.stream_key(65, 1)
+    reqs = []
+    for i in range(args.serve_queries):
+        m = gen.log_uniform_int(key, 4 * i, 2, 512)
+        if gen.draw_int(key, 4 * i + 1) % 10 < 7:
+            name = "rand4" if i % 2 else "english"
+            off = gen.draw_int(key, 4 * i + 2) % (C - m)
+            pat = bytes(specs[name].window(off, m))
+            reqs.append((pat, name, None))
+        else:
+            sg = 4 if i % 2 else 90
+            n = gen.log_uniform_int(key, 4 * i + 3, 4096, 16 << 20)
+            off = gen.draw_int(key, 4 * i + 2) % ((64 << 20) - n)
+            t = pool[sg][off:off + n]
+            pat = bytes(t[(n - m) // 2:(n - m) // 2 + m]) if n > m else bytes(m)
+            reqs.append((pat, None, t))
+    scanned = sum(C if r[1] else len(r[2]) for r in reqs)
+
+    def run_server(arrival_rate=None):
+        srv = Server(corp, budget_bytes=args.serve_budget, streams=4, max_batch=512,
+                     sigma_hints=hints)
+        t0 = time.perf_counter()
+        futs = []
+        if arrival_rate:
+            # Poisson arrivals: every request whose scheduled arrival has
+            # passed is submitted with that time as its arrival (so any lag
+            # of this loop counts as latency), then the loop sleeps.
+            arrive = t0 + np.cumsum(np.random.default_rng(1).exponential(1.0 / arrival_rate, len(reqs)))
+            k = 0
+            while k < len(reqs):
+                now = time.perf_counter()
+                while k < len(reqs) and arrive[k] <= now:
+                    pat, name, own = reqs[k]
+                    futs.append(srv.submit(pat, corpus=name, text=own, t_arrival=float(arrive[k])))
+                    k += 1
+                if k < len(reqs):
+                    time.sleep(min(max(arrive[k] - time.perf_counter(), 0.0), 0.001))
+        else:
+            for pat, name, own in reqs:
+                futs.append(srv.submit(pat, corpus=name, text=own))
+        # Consume results as a client would: keep each result's length and
+        # drop the array, so the pinned copy-back buffers are recycled.
+        lens = []
+        for k in range(len(futs)):
+            lens.append(len(futs[k].result()))
+            futs[k] = None
+        dt = time.perf_counter() - t0
+        srv.close()
+        st = srv.stats()
+        st["seconds"] = round(dt, 3)
+        st["qps"] = round(len(reqs) / dt, 1)
+        return st, lens
+
+    run_server()  # warm-up (allocator, module load)
+    sat, results = run_server()
+    # one launch per query, same queries, synchronous
+    t0 = time.perf_counter()
+    lat1 = []
+    unb_counts = []
+    for pat, name, own in reqs:
+        ts = time.perf_counter()
+        text = corp[name] if name else torch.from_numpy(own).to(dev)
+        pos = smg.search(text, pat).cpu()  # positions delivered to the host, as served
+        unb_counts.append(pos.numel())
+        lat1.append(time.perf_counter() - ts)
+    unb_dt = time.perf_counter() - t0
+    same = all(r == c for r, c in zip(results, unb_counts))
+    loads = {}
+    for frac in args.serve_loads:
+        st, _ = run_server(arrival_rate=frac * sat["qps"])
+        loads[str(frac)] = {"offered_qps": round(frac * sat["qps"], 1), "qps": st["qps"],
+                            "p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
+                            "batches": st["batches"], "host_s": st["host_s"]}
+    out = {
+        "workload": f"serve_{len(reqs)}q_corpus{C}", "metric": "served queries/s, p50/p99 latency",
+        "queries": len(reqs), "scanned_bytes": scanned,
+        "batched": {"qps": sat["qps"], "scanned_GBs": round(scanned / sat["seconds"] / 1e9, 1),
+                    "batches": sat["batches"], "retries": sat["retries"], "host_s": sat["host_s"],
+                    "seconds": sat["seconds"]},
+        "unbatched": {"qps": round(len(reqs) / unb_dt, 1),
+                      "p50_ms": round(float(np.percentile(lat1, 50)) * 1e3, 3),
+                      "p99_ms": round(float(np.percentile(lat1, 99)) * 1e3, 3)},
+        "speedup_qps": round(sat["qps"] / (len(reqs) / unb_dt), 2),
+        "poisson": loads, "counts_match_unbatched": same,
+    }
+    print(json.dumps(out), flush=True)
+
+
 # ---------------------------------------------------------------- reference arm
 
 def run_reference(args, world, rank):
@@ -524,7 +647,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["sweep", "single", "bandwidth"], default="sweep")
+    ap.add_argument("--workload", choices=["sweep", "single", "bandwidth", "serve"], default="sweep")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -534,6 +657,11 @@ def main():
     ap.add_argument("--bw-bytes", type=int, default=8 << 30)
     ap.add_argument("--ms", default="", help="sweep subset: comma-separated pattern lengths")
     ap.add_argument("--per-m", type=int, default=0, help="sweep subset: patterns per (text, m)")
+    ap.add_argument("--serve-queries", type=int, default=4000)
+    ap.add_argument("--serve-corpus", type=int, default=256 << 20)
+    ap.add_argument("--serve-budget", type=int, default=40 << 30)
+    ap.add_argument("--serve-loads", type=float, nargs="*", default=[0.5, 0.8, 0.95])
+    ap.add_argument("--serve-no-unbatched", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -551,6 +679,10 @@ def main():
         if args.workload == "bandwidth":
             if rank == 0:
                 bench_bandwidth(args, world, rank, local)
+            return
+        if args.workload == "serve":
+            if rank == 0:
+                bench_serve(args, world, rank, local)
             return
         out = run_ours(args, world, rank, local)
         if rank == 0:

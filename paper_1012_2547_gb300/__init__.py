@@ -18,7 +18,8 @@ from ._lib import SM_ETRUNC, SmError, VARIANTS, VARIANT_NAMES, check, sm_config,
 
 __all__ = [
     "Plan", "prepare", "prepare_many", "search", "search_into", "search_plan", "search_batch",
-    "batch_workspace_size", "search_batch_async",
+    "batch_workspace_size", "search_batch_async", "query_array", "search_batch_async_array",
+    "batch_workspace_size_array",
     "Batch", "sync", "gen_text", "tuning_get", "tuning_set", "tuning_reset", "kernel_launches",
     "SmError", "SM_ETRUNC", "lib_path",
 ]
@@ -219,6 +220,40 @@ def search_batch_async(items, workspace, stream=None) -> None:
     arr = _queries(items)
     check(_lib.load().sm_search_batch_async(arr, len(items), workspace.data_ptr(), workspace.numel(),
                                             _stream_ptr(stream)), "sm_search_batch_async")
+
+
+def query_array(text_ptrs, ns, plans, out_ptrs, caps, count_ptrs):
+    """An sm_query array built from raw device pointers (uint64 arrays of
+    equal length), without per-query Python objects."""
+    import numpy as np
+    nq = len(ns)
+    a = np.empty((nq, 6), dtype=np.uint64)
+    a[:, 0] = text_ptrs
+    a[:, 1] = ns
+    a[:, 2] = [p.handle for p in plans]
+    a[:, 3] = out_ptrs
+    a[:, 4] = caps
+    a[:, 5] = count_ptrs
+    return a
+
+
+def search_batch_async_array(qarr, workspace_ptr: int, workspace_bytes: int, stream=None) -> None:
+    """sm_search_batch_async on an array from query_array."""
+    if len(qarr) == 0:
+        return
+    ptr = ctypes.cast(qarr.ctypes.data, ctypes.POINTER(sm_query))
+    check(_lib.load().sm_search_batch_async(ptr, len(qarr), workspace_ptr, workspace_bytes,
+                                            _stream_ptr(stream)), "sm_search_batch_async")
+
+
+def batch_workspace_size_array(qarr) -> int:
+    if len(qarr) == 0:
+        return 0
+    out = ctypes.c_size_t()
+    ptr = ctypes.cast(qarr.ctypes.data, ctypes.POINTER(sm_query))
+    check(_lib.load().sm_batch_workspace_size(ptr, len(qarr), ctypes.byref(out)),
+          "sm_batch_workspace_size")
+    return int(out.value)
 
 
 def search_batch(items, stream=None) -> None:

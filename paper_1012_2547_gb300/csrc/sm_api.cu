@@ -16,6 +16,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -42,10 +43,72 @@ namespace {
 constexpr uint32_t kMaxM = 1u << 24;
 constexpr size_t kTicketBytes = 256;  // up to 32 claim counters per launch set
 
+// Device blocks for plans are recycled instead of freed: cudaFree waits for
+// the whole device, which would stall every stream each time a batch's plans
+// are released (e.g. by a serving loop).  Released blocks go to a free list
+// by power-of-two size class (bounded in total bytes); larger requests and
+// overflow use cudaMalloc / cudaFree directly.
+class BlockPool {
+  public:
+    static BlockPool &get() {
+        static BlockPool *P = new BlockPool();  // never destroyed: used at exit
+        return *P;
+    }
+    cudaError_t acquire(size_t bytes, void **out, size_t *cls_bytes) {
+        const size_t cls = size_class(bytes);
+        {
+            std::lock_guard<std::mutex> g(mu_);
+            auto &fl = free_[index(cls)];
+            if (cls <= kMaxClass && !fl.empty()) {
+                *out = fl.back();
+                fl.pop_back();
+                cached_ -= cls;
+                *cls_bytes = cls;
+                return cudaSuccess;
+            }
+        }
+        *cls_bytes = cls;
+        return cudaMalloc(out, cls);
+    }
+    void release(void *p, size_t cls) {
+        if (!p) return;
+        {
+            std::lock_guard<std::mutex> g(mu_);
+            if (cls <= kMaxClass && cached_ + cls <= kMaxCached) {
+                free_[index(cls)].push_back(p);
+                cached_ += cls;
+                return;
+            }
+        }
+        cudaFree(p);
+    }
+
+  private:
+    static constexpr size_t kMinClass = 4096;
+    static constexpr size_t kMaxClass = size_t(64) << 20;
+    static constexpr size_t kMaxCached = size_t(512) << 20;
+    static size_t size_class(size_t b) {
+        size_t c = kMinClass;
+        while (c < b) c <<= 1;
+        return c;
+    }
+    static int index(size_t cls) {
+        int i = 0;
+        while ((kMinClass << i) < cls) ++i;
+        return i;
+    }
+    std::mutex mu_;
+    std::vector<void *> free_[48];
+    size_t cached_ = 0;
+};
+
 struct DevArena {
     void *ptr = nullptr;
+    size_t cls = 0;  // pooled block size (0: plain cudaMalloc)
     ~DevArena() {
-        if (ptr) cudaFree(ptr);
+        if (!ptr) return;
+        if (cls) BlockPool::get().release(ptr, cls);
+        else cudaFree(ptr);
     }
 };
 
@@ -325,28 +388,52 @@ sm_status build_blob(const uint8_t *p, uint32_t m, uint32_t sigma, const sm_conf
 }
 
 sm_status prepare_many(const uint8_t *patterns, const uint32_t *lengths, uint32_t count,
-                       uint32_t sigma, const sm_config *cfg, sm_plan **out) {
+                       uint32_t sigma, const sm_config *cfg, cudaStream_t stream, sm_plan **out) {
     sm_status st = ensure_init();
     if (st != SM_OK) return st;
     std::vector<std::vector<uint8_t>> blobs(count);
     std::vector<PlanDev> hdrs(count);
     std::vector<int> kids(count);
-    size_t total = 0, pos = 0;
+    std::vector<size_t> pat_off(count);
+    size_t pos = 0;
+    for (uint32_t i = 0; i < count; ++i) {
+        if (lengths[i] == 0 || lengths[i] > kMaxM) return SM_EINVAL;
+        pat_off[i] = pos;
+        pos += lengths[i];
+    }
+    // Host tables of many patterns are built on several threads.
+    std::vector<sm_status> sts(count, SM_OK);
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const unsigned nth = static_cast<unsigned>(std::min<uint64_t>(std::min(hw, 16u), (pos >> 14) + 1));
+    auto work = [&](unsigned t) {
+        for (uint32_t i = t; i < count; i += nth)
+            sts[i] = build_blob(patterns + pat_off[i], lengths[i], sigma, cfg, &blobs[i], &hdrs[i], &kids[i]);
+    };
+    if (nth <= 1 || count < 64) {
+        work(0);
+        for (unsigned t = 1; t < nth; ++t) work(t);
+    } else {
+        std::vector<std::thread> pool;
+        for (unsigned t = 1; t < nth; ++t) pool.emplace_back(work, t);
+        work(0);
+        for (auto &th : pool) th.join();
+    }
+    size_t total = 0;
     std::vector<size_t> offs(count);
     for (uint32_t i = 0; i < count; ++i) {
-        const uint32_t m = lengths[i];
-        if (m == 0 || m > kMaxM) return SM_EINVAL;
-        st = build_blob(patterns + pos, m, sigma, cfg, &blobs[i], &hdrs[i], &kids[i]);
-        if (st != SM_OK) return st;
+        if (sts[i] != SM_OK) return sts[i];
         offs[i] = total;
         total += blobs[i].size();
-        pos += m;
     }
     std::vector<uint8_t> host(total);
     for (uint32_t i = 0; i < count; ++i) std::memcpy(host.data() + offs[i], blobs[i].data(), blobs[i].size());
     auto arena = std::make_shared<DevArena>();
-    SM_TRY_CUDA(cudaMalloc(&arena->ptr, std::max<size_t>(total, 256)));
-    SM_TRY_CUDA(cudaMemcpy(arena->ptr, host.data(), total, cudaMemcpyHostToDevice));
+    SM_TRY_CUDA(BlockPool::get().acquire(std::max<size_t>(total, 256), &arena->ptr, &arena->cls));
+    // Upload on the caller's stream, then wait for it: the plans are usable
+    // by work on any stream once this returns, and no legacy-default-stream
+    // copy serialises with other streams' work.
+    SM_TRY_CUDA(cudaMemcpyAsync(arena->ptr, host.data(), total, cudaMemcpyHostToDevice, stream));
+    SM_TRY_CUDA(cudaStreamSynchronize(stream));
     pos = 0;
     for (uint32_t i = 0; i < count; ++i) {
         sm_plan *pl = new sm_plan();
@@ -659,9 +746,8 @@ extern "C" {
 
 sm_status sm_prepare_ex(const uint8_t *pattern, uint32_t m, uint32_t sigma_hint,
                         const sm_config *config, sm_stream_t stream, sm_plan **out_plan) {
-    (void)stream;
     if (!pattern || !out_plan || m == 0 || m > kMaxM) return SM_EINVAL;
-    return prepare_many(pattern, &m, 1, sigma_hint, config, out_plan);
+    return prepare_many(pattern, &m, 1, sigma_hint, config, stream, out_plan);
 }
 
 sm_status sm_prepare(const uint8_t *pattern, uint32_t m, uint32_t sigma_hint, sm_stream_t stream,
@@ -672,10 +758,9 @@ sm_status sm_prepare(const uint8_t *pattern, uint32_t m, uint32_t sigma_hint, sm
 sm_status sm_prepare_many(const uint8_t *patterns, const uint32_t *lengths, uint32_t count,
                           uint32_t sigma_hint, const sm_config *config, sm_stream_t stream,
                           sm_plan **out_plans) {
-    (void)stream;
     if (count == 0) return SM_OK;
     if (!patterns || !lengths || !out_plans) return SM_EINVAL;
-    return prepare_many(patterns, lengths, count, sigma_hint, config, out_plans);
+    return prepare_many(patterns, lengths, count, sigma_hint, config, stream, out_plans);
 }
 
 sm_status sm_plan_free(sm_plan *plan) {

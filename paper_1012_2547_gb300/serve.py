@@ -15,8 +15,9 @@ thread repeatedly
      oldest pending request) in arrival order, up to ``max_batch``;
   3. launches the batch on a free stream with ``sm_search_batch_async``
      (one persistent launch per kernel family, in memory the server owns),
-     followed by the device-to-host copies of counts and positions and an
-     event.
+     followed by the copy of the counts and an event; once the counts are
+     on the host, exactly the valid positions of each request are copied
+     back (a second event).
 
 Up to ``streams`` batches are in flight at once, so requests that arrive
 while others run are admitted as slots and memory free up and their work
@@ -67,8 +68,10 @@ class Policy:
     """Host-side scheduling decisions.  No GPU work."""
 
     def __init__(self, budget_bytes: int, max_batch: int = 512, max_wait: float = 0.0005,
-                 corpus_bytes=None, workspace_per_batch: int = 128 << 20):
+                 corpus_bytes=None, workspace_per_batch: int = 128 << 20,
+                 max_batch_out_bytes: int = 1 << 62):
         self.budget = int(budget_bytes)
+        self.max_batch_out = int(max_batch_out_bytes)
         self.max_batch = int(max_batch)
         self.max_wait = float(max_wait)
         self.used = 0
@@ -104,12 +107,15 @@ class Policy:
         if self.used + reserved > self.budget:
             return [], 0, rejected
         keep = collections.deque()
+        out_bytes = 0
         while self.pending and len(batch) < self.max_batch:
             r = self.pending.popleft()
             need = self.need(r)
-            if length_class(r.m) == cls and self.used + reserved + need <= self.budget:
+            fits_out = not batch or out_bytes + 8 * r.cap <= self.max_batch_out
+            if length_class(r.m) == cls and self.used + reserved + need <= self.budget and fits_out:
                 batch.append(r)
                 reserved += need
+                out_bytes += 8 * r.cap
             else:
                 keep.append(r)
                 if self.used + reserved + need > self.budget and length_class(r.m) == cls:
@@ -130,7 +136,8 @@ class Server:
 
     def __init__(self, corpora: dict, budget_bytes: int = 40 << 30, streams: int = 4,
                  max_batch: int = 512, max_wait: float = 0.0005, first_cap: int = 256,
-                 sigma_hints: dict | None = None, own_text_sigma: int = 0):
+                 sigma_hints: dict | None = None, own_text_sigma: int = 0,
+                 staging_bytes: int = 256 << 20):
         import torch
 
         import paper_1012_2547_gb300 as smg
@@ -141,13 +148,20 @@ class Server:
         self.own_text_sigma = own_text_sigma
         self.first_cap = int(first_cap)
         self.policy = Policy(budget_bytes, max_batch, max_wait,
-                             {k: v.numel() for k, v in self.corpora.items()})
+                             {k: v.numel() for k, v in self.corpora.items()},
+                             max_batch_out_bytes=staging_bytes)
         self.streams = [torch.cuda.Stream() for _ in range(streams)]
         self.inflight: list[dict | None] = [None] * streams
+        # Per-stream pinned staging for copy-back, allocated up front: a
+        # batch's outputs fit it (Policy caps them), except a single larger
+        # request, for which it grows once.
+        self._staging: list = [torch.empty(max(staging_bytes // 8, 1), dtype=torch.int64, pin_memory=True)
+                               for _ in range(streams)]
         self.latencies: list[float] = []
         self.completed = 0
         self.retries = 0
         self.batches = 0
+        self.host_s = collections.Counter()  # host seconds per scheduler phase
         self._ids = itertools.count()
         self._lock = threading.Lock()
         self._wake = threading.Event()
@@ -158,7 +172,8 @@ class Server:
 
     # ---------------------------------------------------------------- API
 
-    def submit(self, pattern, corpus: str | None = None, text=None) -> cf.Future:
+    def submit(self, pattern, corpus: str | None = None, text=None,
+               t_arrival: float | None = None) -> cf.Future:
         p = bytes(pattern)
         if not p:
             raise ValueError("empty pattern")
@@ -170,12 +185,23 @@ class Server:
                                                           if isinstance(text, (bytes, bytearray))
                                                           else text, dtype=np.uint8)
         n = len(t) if t is not None else self.corpora[corpus].numel()
-        r = Request(next(self._ids), p, corpus, t, min(self.first_cap, max(n - len(p) + 1, 1)),
-                    time.perf_counter())
+        r = Request(next(self._ids), p, corpus, t, self._first_cap(n, len(p), corpus),
+                    time.perf_counter() if t_arrival is None else t_arrival)
         with self._lock:
             self.policy.push(r)
         self._wake.set()
         return r.future
+
+    def _first_cap(self, n: int, m: int, corpus: str | None) -> int:
+        """Output capacity of a first attempt: for a corpus with an alphabet
+        hint, twice the count expected on a uniform text, (n-m+1)/sigma^m,
+        plus first_cap; else first_cap.  A larger true count costs a retry."""
+        starts = max(n - m + 1, 1)
+        sigma = self.sigma_hints.get(corpus, 0) if corpus is not None else self.own_text_sigma
+        cap = self.first_cap
+        if sigma >= 2 and m * np.log2(sigma) < 62:
+            cap += int(2 * starts / float(sigma) ** m)
+        return min(cap, starts)
 
     def close(self, timeout: float | None = None) -> None:
         self._stop = True
@@ -187,7 +213,8 @@ class Server:
     def stats(self) -> dict:
         lat = np.array(self.latencies) if self.latencies else np.zeros(1)
         return {"completed": self.completed, "batches": self.batches, "retries": self.retries,
-                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3)}
+                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "host_s": {k: round(v, 4) for k, v in self.host_s.items()}}
 
     # ---------------------------------------------------------------- loop
 
@@ -227,6 +254,7 @@ class Server:
         torch, smg = self._torch, self._smg
         s = self.streams[slot]
         dev = torch.device("cuda")
+        t0 = time.perf_counter()
         with torch.cuda.stream(s):
             texts = []
             for r in batch:
@@ -234,25 +262,57 @@ class Server:
                     texts.append(torch.from_numpy(r.text).to(dev, non_blocking=False))
                 else:
                     texts.append(self.corpora[r.corpus])
+            t1 = time.perf_counter()
             hint = self.sigma_hints.get(batch[0].corpus, self.own_text_sigma)
             plans = smg.prepare_many([r.pattern for r in batch], sigma_hint=hint)
+            t2 = time.perf_counter()
             caps = np.array([r.cap for r in batch], dtype=np.int64)
             offs = np.concatenate([[0], np.cumsum(caps)])
             out = torch.empty(int(offs[-1]) or 1, dtype=torch.int64, device=dev)
             cnt = torch.empty(len(batch), dtype=torch.int64, device=dev)
-            items = [(texts[i], plans[i], out[int(offs[i]):int(offs[i + 1])], cnt[i:i + 1])
-                     for i in range(len(batch))]
-            ws = torch.empty(max(smg.batch_workspace_size(items), 256), dtype=torch.uint8, device=dev)
-            smg.search_batch_async(items, ws, stream=s)
+            qarr = smg.query_array(
+                np.array([t.data_ptr() for t in texts], dtype=np.uint64),
+                np.array([t.numel() for t in texts], dtype=np.uint64), plans,
+                np.uint64(out.data_ptr()) + 8 * offs[:-1].astype(np.uint64), caps.astype(np.uint64),
+                np.uint64(cnt.data_ptr()) + 8 * np.arange(len(batch), dtype=np.uint64))
+            need = max(smg.batch_workspace_size_array(qarr), 256)
+            ws = torch.empty(need, dtype=torch.uint8, device=dev)
+            smg.search_batch_async_array(qarr, ws.data_ptr(), need, stream=s)
             cnt_h = torch.empty(len(batch), dtype=torch.int64, pin_memory=True)
-            out_h = torch.empty(out.numel(), dtype=torch.int64, pin_memory=True)
             cnt_h.copy_(cnt, non_blocking=True)
-            out_h.copy_(out, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(s)
-        self.inflight[slot] = {"batch": batch, "event": ev, "cnt_h": cnt_h, "out_h": out_h,
-                               "offs": offs, "keep": (texts, plans, out, cnt, ws), "reserved": reserved}
+        t3 = time.perf_counter()
+        self.host_s["h2d_own_texts"] += t1 - t0
+        self.host_s["prepare"] += t2 - t1
+        self.host_s["launch"] += t3 - t2
+        self.inflight[slot] = {"batch": batch, "event": ev, "cnt_h": cnt_h, "out_h": None,
+                               "offs": offs, "keep": (texts, plans, out, cnt, ws), "reserved": reserved,
+                               "phase": 0}
         self.batches += 1
+
+    def _copy_back(self, i: int, rec: dict) -> None:
+        """Counts are on the host: copy back exactly the valid positions of
+        each complete request (not the whole capacity), then an event."""
+        torch = self._torch
+        counts = rec["cnt_h"].numpy()
+        caps = np.array([r.cap for r in rec["batch"]], dtype=np.int64)
+        take = np.where(counts <= caps, counts, 0)
+        dst_offs = np.concatenate([[0], np.cumsum(take)])
+        need = max(int(dst_offs[-1]), 1)
+        if self._staging[i] is None or self._staging[i].numel() < need:
+            self._staging[i] = torch.empty(max(need + need // 4, 1 << 20), dtype=torch.int64,
+                                           pin_memory=True)
+        out_h = self._staging[i]
+        out = rec["keep"][2]
+        s = self.streams[i]
+        with torch.cuda.stream(s):
+            for j in np.flatnonzero(take):
+                a = int(rec["offs"][j])
+                out_h[int(dst_offs[j]):int(dst_offs[j + 1])].copy_(out[a:a + int(take[j])], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(s)
+        rec.update(out_h=out_h, dst_offs=dst_offs, event=ev, phase=1)
 
     def _retire(self) -> bool:
         done_any = False
@@ -260,10 +320,15 @@ class Server:
             if rec is None or not rec["event"].query():
                 continue
             done_any = True
+            if rec["phase"] == 0:
+                tc = time.perf_counter()
+                self._copy_back(i, rec)
+                self.host_s["copy_back"] += time.perf_counter() - tc
+                continue
             now = time.perf_counter()
             counts = rec["cnt_h"].numpy()
             out_h = rec["out_h"].numpy()
-            offs = rec["offs"]
+            offs = rec["dst_offs"]
             requeue = []
             for j, r in enumerate(rec["batch"]):
                 c = int(counts[j])
@@ -272,7 +337,11 @@ class Server:
                     r.attempts += 1
                     requeue.append(r)
                     continue
-                pos = out_h[int(offs[j]):int(offs[j]) + c].astype(np.uint64)
+                # Copied out of the stream's reusable pinned staging buffer
+                # (torch's CPU copy runs on several threads).
+                res = self._torch.empty(c, dtype=self._torch.int64)
+                res.copy_(rec["out_h"][int(offs[j]):int(offs[j]) + c])
+                pos = res.numpy().view(np.uint64)
                 self.latencies.append(now - r.t_arrival)
                 self.completed += 1
                 r.future.set_result(pos)
@@ -284,4 +353,5 @@ class Server:
                     self.policy.push(r, front=True)
                 self.retries += len(requeue)
                 self.inflight[i] = None
+            self.host_s["retire"] += time.perf_counter() - now
         return done_any

@@ -50,6 +50,19 @@ def test_admission_respects_budget_and_rejects_impossible():
     assert b3 and b3[0].rid == b[-1].rid + 1
 
 
+def test_batch_output_cap():
+    p = Policy(budget_bytes=1 << 40, max_batch=100, workspace_per_batch=0, max_batch_out_bytes=8 * 100)
+    for i, cap in enumerate([60, 30, 20, 500, 10]):
+        r = req(i, 8, cap=cap)
+        p.push(r)
+    b, _, _ = p.take()
+    assert [r.rid for r in b] == [0, 1, 4]                   # 60 + 30 + 10 <= 100 positions
+    b2, _, _ = p.take()
+    assert [r.rid for r in b2] == [2]
+    b3, _, _ = p.take()
+    assert [r.rid for r in b3] == [3]                        # alone, though above the cap
+
+
 def test_ready_rules():
     p = Policy(budget_bytes=1 << 30, max_batch=2, max_wait=0.01)
     assert not p.ready(0.0, busy=0)

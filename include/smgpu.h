@@ -75,8 +75,11 @@ typedef struct sm_batch sm_batch; /* opaque, library-owned */
  *   variant  : sm_variant.
  *   q        : q-gram length for SM_VARIANT_QGRAM, 1..8 and <= m.
  *   word_bits: Shift-Or state width, 32 or 64 (m <= 32 or m <= 64).
- *   tile     : log2 hint of the work-item size for QGRAM/LINEAR (ignored
- *              by SHIFTOR, whose tile is fixed by its kernel shape).
+ *   tile     : log2 hint of the work-item size.  QGRAM/LINEAR: bytes of
+ *              start positions per thread range.  SHIFTOR (whose staged
+ *              sub-tile is fixed at 4,608 end positions): the shortest work
+ *              item in bytes, rounded up to whole sub-tiles and capped at 64
+ *              of them; 0 lets the launch size items from the grid alone.
  */
 typedef struct {
     uint32_t variant;

@@ -216,6 +216,7 @@ struct sm_plan {
     const PlanDev *dev = nullptr;
     std::shared_ptr<DevArena> arena;
     int kid = 0;
+    uint32_t min_units = 1;  // shortest work item in units (config `tile`, bit-parallel kernels)
     std::vector<uint8_t> pattern;
 };
 
@@ -240,7 +241,8 @@ namespace {
 
 // Host blob for one pattern.  Returns SM_EINVAL if `cfg` cannot serve it.
 sm_status build_blob(const uint8_t *p, uint32_t m, uint32_t sigma, const sm_config *cfg,
-                     std::vector<uint8_t> *blob, PlanDev *hdr_out, int *kid_out) {
+                     std::vector<uint8_t> *blob, PlanDev *hdr_out, int *kid_out,
+                     uint32_t *min_units_out) {
     Lib &L = lib();
     sm_config tc{};
     {
@@ -269,6 +271,12 @@ sm_status build_blob(const uint8_t *p, uint32_t m, uint32_t sigma, const sm_conf
         h.variant = VAR_SHIFTOR;
         h.word_bits = wb;
         h.tile_starts = static_cast<uint32_t>(so_tile_starts());
+        // tile: log2 of the shortest work item in bytes, whole sub-tiles.
+        if (src->tile) {
+            const uint64_t bytes = 1ull << std::min(src->tile, 40u);
+            *min_units_out = static_cast<uint32_t>(std::min<uint64_t>(
+                so_max_sub(), std::max<uint64_t>(1, (bytes + so_tile_starts() - 1) / so_tile_starts())));
+        }
     } else if (variant == SM_VARIANT_QGRAM) {
         q = src->q ? src->q : rule_q(m, sigma);
         if (!explicit_cfg) q = std::min(q, m);
@@ -394,6 +402,7 @@ sm_status prepare_many(const uint8_t *patterns, const uint32_t *lengths, uint32_
     std::vector<std::vector<uint8_t>> blobs(count);
     std::vector<PlanDev> hdrs(count);
     std::vector<int> kids(count);
+    std::vector<uint32_t> min_units(count, 1);
     std::vector<size_t> pat_off(count);
     size_t pos = 0;
     for (uint32_t i = 0; i < count; ++i) {
@@ -407,7 +416,8 @@ sm_status prepare_many(const uint8_t *patterns, const uint32_t *lengths, uint32_
     const unsigned nth = static_cast<unsigned>(std::min<uint64_t>(std::min(hw, 16u), (pos >> 14) + 1));
     auto work = [&](unsigned t) {
         for (uint32_t i = t; i < count; i += nth)
-            sts[i] = build_blob(patterns + pat_off[i], lengths[i], sigma, cfg, &blobs[i], &hdrs[i], &kids[i]);
+            sts[i] = build_blob(patterns + pat_off[i], lengths[i], sigma, cfg, &blobs[i], &hdrs[i], &kids[i],
+                                &min_units[i]);
     };
     if (nth <= 1 || count < 64) {
         work(0);
@@ -441,6 +451,7 @@ sm_status prepare_many(const uint8_t *patterns, const uint32_t *lengths, uint32_
         pl->dev = reinterpret_cast<const PlanDev *>(static_cast<uint8_t *>(arena->ptr) + offs[i]);
         pl->arena = arena;
         pl->kid = kids[i];
+        pl->min_units = min_units[i];
         pl->pattern.assign(patterns + pos, patterns + pos + lengths[i]);
         pos += lengths[i];
         out[i] = pl;
@@ -475,13 +486,15 @@ int grid_for(int kid, uint64_t tickets) {
 }
 
 // Units per work item for a launch that covers `units` units (staged
-// sub-tiles of the bit-parallel kernels, base ranges of the others): about four work items per resident block, so a
-// large launch gets long work items (their look-backs then find an
-// inclusive predecessor at once) and a small one keeps every block busy.
+// sub-tiles of the bit-parallel kernels, base ranges of the others): at most
+// four work items per resident block, rounded so that the last round of
+// items fills the grid (a round with a few items would leave most blocks
+// idle for a whole item); a large launch gets long work items and a small
+// one keeps every block busy.
 uint32_t sub_per_item(int kid, uint64_t units) {
     const KernelShape &s = lib().shapes[kid];
     const uint64_t resident = static_cast<uint64_t>(lib().sms) * std::max(1, s.blocks_per_sm);
-    const uint64_t per = units / (4 * resident);
+    const uint64_t per = (units + 4 * resident - 1) / (4 * resident);
     const uint64_t cap = so_kid(kid) ? std::min<uint64_t>(lib().item_cap, so_max_sub())
                                         : lib().item_cap;
     return static_cast<uint32_t>(std::max<uint64_t>(1, std::min<uint64_t>(cap, per)));
@@ -576,7 +589,7 @@ sm_status search_plan_impl(const sm_plan *plan, const uint8_t *text, uint64_t n,
         SM_TRY_CUDA(cudaMemsetAsync(out_count, 0, sizeof(uint64_t), stream));
         return SM_OK;
     }
-    const uint32_t per = balanced_per(units, sub_per_item(plan->kid, units));
+    const uint32_t per = balanced_per(units, std::max(sub_per_item(plan->kid, units), plan->min_units));
     const uint64_t ntiles = (units + per - 1) / per;
     const int grid = grid_for(plan->kid, ntiles);
     const size_t reset = align16(kTicketBytes + ntiles * sizeof(uint64_t));
@@ -644,7 +657,7 @@ sm_status batch_layout(const sm_query *qs, uint32_t nq, uint8_t *base, sm_batch 
     std::vector<uint32_t> per_q(nq, 1);
     for (uint32_t i = 0; i < nq; ++i) {
         if (units[i] == 0) continue;
-        per_q[i] = balanced_per(units[i], group_per[qs[i].plan->kid]);
+        per_q[i] = balanced_per(units[i], std::max(group_per[qs[i].plan->kid], qs[i].plan->min_units));
         ntiles[i] = (units[i] + per_q[i] - 1) / per_q[i];
     }
     uint64_t total_states = 0;

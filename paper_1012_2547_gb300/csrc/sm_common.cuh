@@ -183,15 +183,19 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
 // so successors stop waiting.
 constexpr int LB_WINDOWS = 8;
 
-__device__ __forceinline__ uint64_t lookback_exclusive(uint64_t *state, uint64_t k, uint64_t agg,
-                                                       uint32_t *err, bool *ok) {
+// Publishes item k's own count: inclusive at once for item 0, an aggregate
+// otherwise.  (Whole warp; lane 0 stores.)
+__device__ __forceinline__ void lookback_publish(uint64_t *state, uint64_t k, uint64_t agg) {
+    if ((threadIdx.x & 31) == 0) st_relaxed(&state[k], (k == 0 ? LB_INC : LB_AGG) | agg);
+}
+
+// Exclusive prefix of item k, whose count `agg` lookback_publish has
+// already made visible; publishes the inclusive prefix when found.
+__device__ __forceinline__ uint64_t lookback_resolve(uint64_t *state, uint64_t k, uint64_t agg,
+                                                     uint32_t *err, bool *ok) {
     const int lane = threadIdx.x & 31;
     *ok = true;
-    if (k == 0) {
-        if (lane == 0) st_relaxed(&state[0], LB_INC | agg);
-        return 0;
-    }
-    if (lane == 0) st_relaxed(&state[k], LB_AGG | agg);
+    if (k == 0) return 0;
     uint64_t excl = 0;
     int64_t j = static_cast<int64_t>(k) - 1;  // nearest predecessor not yet summed
     int nwin = 1;
@@ -259,6 +263,13 @@ __device__ __forceinline__ uint64_t lookback_exclusive(uint64_t *state, uint64_t
     }
     if (lane == 0) st_relaxed(&state[k], LB_INC | ((excl + agg) & LB_VAL));
     return excl;
+}
+
+// Publish and resolve in one go (the item's warp waits for its prefix).
+__device__ __forceinline__ uint64_t lookback_exclusive(uint64_t *state, uint64_t k, uint64_t agg,
+                                                       uint32_t *err, bool *ok) {
+    lookback_publish(state, k, agg);
+    return lookback_resolve(state, k, agg, err, ok);
 }
 
 // Ticket -> (query index, tile) for a launch.

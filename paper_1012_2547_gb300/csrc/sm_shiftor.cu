@@ -50,10 +50,21 @@ constexpr uint32_t SO_BUF = SO_LHALO + SO_T;
 #define SO_NBUF_SLOTS 3
 #endif
 constexpr int SO_NBUF = SO_NBUF_SLOTS;      // staging ring: SO_NBUF-1 sub-tiles in flight while one is scanned
-constexpr int SO_HITS = 512;                // hits of one work item kept in shared memory
+// Hits of one work item kept in shared memory (two buffers).  Zero: every
+// hit goes to the spill area (L2-resident), which leaves the shared memory
+// to the staging ring and lets 15 one-warp blocks share an SM.
+#ifndef SO_HIT_SLOTS
+#define SO_HIT_SLOTS 0
+#endif
+constexpr int SO_HITS = SO_HIT_SLOTS;
 constexpr uint32_t SO_MAX_SUB = 64;         // most sub-tiles per work item
 constexpr uint32_t SO_SUB_FLAGS = SO_SEGC * 32 * 2;            // 16-bit flags of a sub-tile
-constexpr uint32_t SO_SPILL_BYTES = SO_MAX_SUB * SO_SUB_FLAGS;  // per block
+// Spill area of one item: a list of item-relative positions (4 bytes per
+// hit: cheaper than flag words below about one hit per 32 bytes), then the
+// flag words of the sub-tiles that follow once the list is full.
+constexpr uint32_t SO_SPILL_POS = 4096;
+constexpr uint32_t SO_SPILL_ITEM = SO_SPILL_POS * 4 + SO_MAX_SUB * SO_SUB_FLAGS;
+constexpr uint32_t SO_SPILL_BYTES = 2 * SO_SPILL_ITEM;          // per block (two items)
 
 // Dynamic shared memory of a block: the staging ring, the item hit buffer,
 // mbarriers and two run-time constants.  The mask table is a static
@@ -62,7 +73,7 @@ constexpr uint32_t SO_SPILL_BYTES = SO_MAX_SUB * SO_SUB_FLAGS;  // per block
 template <typename Entry>
 struct SOLayout {
     static constexpr uint32_t HITS_OFF = SO_NBUF * SO_BUF;
-    static constexpr uint32_t BAR_OFF = HITS_OFF + SO_HITS * 4;
+    static constexpr uint32_t BAR_OFF = HITS_OFF + 2 * SO_HITS * 4;  // two hit buffers
     static constexpr uint32_t CONST_OFF = BAR_OFF + 8 * SO_NBUF;  // multipliers the compiler cannot fold
     static constexpr uint32_t BYTES = CONST_OFF + 16;
 };
@@ -299,26 +310,96 @@ __device__ __forceinline__ bool so_claim(const LaunchArgs &a, unsigned long long
     return true;
 }
 
+// A scanned work item whose hits wait in one of the two hit buffers (and
+// spill areas) until its prefix is known.  All fields are warp-uniform.
+struct SOItem {
+    uint32_t qi;
+    uint64_t k, sb, se;       // item index, sub-tile range [sb, se)
+    uint32_t count;           // hits of the item
+    uint32_t buffered;        // hits in the shared buffer
+    uint32_t listed;          // hits in the spill area's position list
+    uint64_t flag_from;       // first sub-tile whose flag words were spilled (se: none)
+};
+
+// Loads plan P's mask table into shared memory unless it is there already.
+template <typename Entry>
+__device__ __forceinline__ void so_table(const PlanDev *P, const PlanDev *&cur_plan, uint8_t *tbl,
+                                         uint32_t &m) {
+    if (P == cur_plan) return;
+    __syncwarp();  // no lane still reads the old table
+    const uint4 *src = reinterpret_cast<const uint4 *>(reinterpret_cast<const uint8_t *>(P) +
+                                                       __ldg(&P->off_tbl));
+    for (int c = threadIdx.x & 31; c < static_cast<int>(256 * sizeof(Entry) / 16); c += 32)
+        reinterpret_cast<uint4 *>(tbl)[c] = __ldg(&src[c]);
+    cur_plan = P;
+    m = __ldg(&P->m);
+    __syncwarp();
+}
+
+// Scan of one sub-tile staged at `buf` (its 64 preceding bytes included):
+// flags of the lane's segment, masked to the valid ends.  `carry` is the
+// exact state before the sub-tile (fix-up form only).
+template <typename Word, typename Entry, bool HIST, int WARM>
+__device__ __forceinline__ uint32_t so_subtile(const uint8_t *buf, uint32_t tb, uint32_t m,
+                                               uint32_t two, uint32_t esz, Word &carry,
+                                               bool warm_carry, int elo, int ehi,
+                                               uint32_t (&F)[SO_SEGC]) {
+    const int lane = threadIdx.x & 31;
+    const uint8_t *seg = buf + lane * SO_S;
+    if (WARM) {
+        so_local<Word, Entry, HIST>(seg, so_warmup<Word, Entry, WARM>(seg, tb, two, esz), tb, m, two,
+                                    esz, F);
+    } else {
+        if (warm_carry && lane == 0) carry = so_warm<Word, Entry>(buf - (m - 1), tb, m, esz);
+        const Word Dend = so_local<Word, Entry, HIST>(seg, Word(0), tb, m, two, esz, F);
+        Word Dprev = __shfl_up_sync(0xffffffffu, Dend, 1);
+        if (lane == 0) Dprev = carry;
+        so_fixup<Word, Entry>(seg, tb, m, esz, Dprev, F);
+        carry = __shfl_sync(0xffffffffu, Dend, 31);
+    }
+    return so_mask_count(F, elo, ehi);
+}
+
+// Writes the flagged positions of a lane segment at out[idx...] (capped).
+__device__ __forceinline__ void so_write_flags(const uint32_t (&F)[SO_SEGC], uint64_t idx, uint64_t cap,
+                                               uint64_t *out, int64_t start0) {
+#pragma unroll
+    for (int c = 0; c < SO_SEGC; ++c) {
+        uint32_t f = F[c];
+        while (f) {
+            const int r = 31 - __clz(f);
+            f ^= 1u << r;
+            if (idx < cap) out[idx] = static_cast<uint64_t>(start0 + 16 * c + 15 - r);
+            ++idx;
+        }
+    }
+}
+
 // One warp per block.  The warp claims work items (query, item); an item
 // is `sub_per_item` consecutive sub-tiles of 32 * 144 end positions, staged
-// by bulk copies through a double buffer.  Per sub-tile every lane scans
-// its 144 bytes from the empty state, then patches the occurrences that
-// cross into its segment from the exact state of the previous segment
-// (previous lane, previous sub-tile, or a warm-up over the 64 staged bytes
-// before the item).  Hits of an item are buffered, the item's offset comes
-// from a decoupled look-back, and the buffer is copied out coalesced; an
-// item with more hits than the buffer holds is rescanned and written
-// directly.
+// by bulk copies through an SO_NBUF-slot ring.  Per sub-tile every lane
+// scans its 144 bytes (after a warm-up over the bytes before it, or from
+// the empty state plus a fix-up from the previous segment's exact state).
+// Hits of an item go to shared memory (up to SO_HITS) and then to a
+// per-block spill area, as a position list while they are sparse and as the
+// sub-tiles' flag words once the list is full.  The item's count is
+// published at once and the warp goes on to the next item; its prefix is
+// resolved by decoupled look-back one item later -- by then every earlier
+// item has been scanned, so the look-back rarely waits -- and the hits are
+// copied out.  Two hit buffers and two spill areas alternate between the
+// item being scanned and the item waiting for its prefix.  Without a spill
+// area an item whose hits overflow the buffer is rescanned at write time.
 template <typename Word, typename Entry, bool HIST, int WARM>
 __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchArgs a) {
     using L = SOLayout<Entry>;
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(256) uint8_t tbl[256 * sizeof(Entry)];
     const uint32_t tb = smem_addr(tbl);
-    uint32_t *hits = reinterpret_cast<uint32_t *>(smem + L::HITS_OFF);
+    uint32_t *hits_base = reinterpret_cast<uint32_t *>(smem + L::HITS_OFF);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L::BAR_OFF);
     const int lane = threadIdx.x;
-    uint8_t *spill = a.spill ? a.spill + static_cast<size_t>(blockIdx.x) * SO_SPILL_BYTES : nullptr;
+    uint8_t *spill_base =
+        a.spill ? a.spill + static_cast<size_t>(blockIdx.x) * SO_SPILL_BYTES : nullptr;
 
     unsigned long long t = 0;
     uint32_t qi = 0;
@@ -335,6 +416,8 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
             const uint64_t s1 = min(s0 + Q.sub_per_item, Q.nsub);
             for (int i = 0; i < SO_NBUF - 1 && s0 + i < s1; ++i)
                 so_issue(smem + i * SO_BUF, &bar[i], Q.text, Q.n, s0 + i);
+        } else {
+            t = a.total;
         }
     }
     __syncwarp();
@@ -348,21 +431,93 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
     uint32_t m = 1;
     uint32_t parity = 0;  // bit b: parity of the next phase of bar[b]
     int cur = 0;          // ring slot holding the next sub-tile to scan
-    unsigned long long nt = 0;
-    uint32_t nqi = 0;
-    uint64_t nk = 0;
-    while (t < a.total) {
-        const QueryDev &Q = query_of(a, qi);
-        const PlanDev *P = Q.plan;
-        if (P != cur_plan) {
-            const uint4 *src = reinterpret_cast<const uint4 *>(reinterpret_cast<const uint8_t *>(P) +
-                                                               __ldg(&P->off_tbl));
-            for (int c = lane; c < static_cast<int>(256 * sizeof(Entry) / 16); c += 32)
-                reinterpret_cast<uint4 *>(tbl)[c] = __ldg(&src[c]);  // ordered before the scan by __syncwarp
-            cur_plan = P;
-            m = __ldg(&P->m);
+    int hb = 0;           // hit buffer / spill area of the item being scanned
+    bool have_pending = false;
+    SOItem pend{};
+
+    // Prefix of the pending item, then its hits to the output (capped).
+    auto write_pending = [&]() {
+        const QueryDev &Q = query_of(a, pend.qi);
+        bool ok;
+        const uint64_t excl = lookback_resolve(Q.state, pend.k, pend.count, a.err, &ok);
+        if (!ok) return;
+        if (lane == 0 && pend.k + 1 == Q.ntiles) *Q.out_count = excl + pend.count;
+        const uint64_t cap = Q.cap;
+        if (excl >= cap) return;
+        uint64_t *out = Q.out_pos;
+        const uint8_t *const qtext = Q.text;
+        const uint32_t pm = __ldg(&Q.plan->m);
+        const int64_t o = static_cast<int64_t>(reinterpret_cast<uintptr_t>(qtext) & 15u);
+        const int64_t shift = static_cast<int64_t>(pm) - 1 + o;  // end -> real start
+        const int64_t ivstart = static_cast<int64_t>(pend.sb) * SO_T;
+        const uint32_t *hits = hits_base + (hb ^ 1) * SO_HITS;
+        const bool direct = pend.buffered + pend.listed == pend.count || pend.flag_from < pend.se;
+        if (direct) {
+            for (uint32_t r = lane; r < pend.buffered; r += 32) {
+                const uint64_t idx = excl + r;
+                if (idx < cap) out[idx] = static_cast<uint64_t>(ivstart + hits[r] - shift);
+            }
+            const uint8_t *spill = spill_base + (hb ^ 1) * SO_SPILL_ITEM;
+            const uint32_t *list = reinterpret_cast<const uint32_t *>(spill);
+            for (uint32_t r = lane; r < pend.listed; r += 32) {
+                const uint64_t idx = excl + pend.buffered + r;
+                if (idx < cap) out[idx] = static_cast<uint64_t>(ivstart + list[r] - shift);
+            }
+            const uint8_t *flags = spill + SO_SPILL_POS * 4;
+            uint64_t run = excl + pend.buffered + pend.listed;
+            for (uint64_t s = pend.flag_from; s < pend.se && run < cap; ++s) {
+                const uint16_t *src =
+                    reinterpret_cast<const uint16_t *>(flags + (s - pend.flag_from) * SO_SUB_FLAGS);
+                uint32_t F[SO_SEGC];
+                uint32_t cnt = 0;
+#pragma unroll
+                for (int c = 0; c < SO_SEGC; ++c) {
+                    F[c] = src[c * 32 + lane];
+                    cnt += __popc(F[c]);
+                }
+                uint32_t total;
+                const uint64_t idx = run + warp_excl_scan(cnt, &total);
+                so_write_flags(F, idx, cap, out, static_cast<int64_t>(s) * SO_T + lane * SO_S - shift);
+                run += total;
+            }
+            return;
+        }
+        // Too many hits to buffer and no spill area: rescan the item in the
+        // ring slot that no prefetch uses, writing each sub-tile's hits at
+        // their final offsets.
+        so_table<Entry>(Q.plan, cur_plan, tbl, m);
+        const uint64_t qn = Q.n;
+        const int64_t vlo = o + static_cast<int64_t>(m) - 1;
+        const int64_t vhi = o + static_cast<int64_t>(qn);
+        const int wb = cur == 0 ? SO_NBUF - 1 : cur - 1;
+        uint64_t run = excl;
+        Word carry = 0;
+        for (uint64_t s = pend.sb; s < pend.se && run < cap; ++s) {
+            if (lane == 0) so_issue(smem + wb * SO_BUF, &bar[wb], qtext, qn, s);
+            const bool arrived = mbar_wait_bounded(&bar[wb], (parity >> wb) & 1u);
+            parity ^= 1u << wb;
+            if (!__all_sync(0xffffffffu, arrived)) {
+                if (lane == 0) atomicOr(a.err, ERR_COPY);
+                break;
+            }
+            const int64_t x = static_cast<int64_t>(s) * SO_T + lane * SO_S;
+            const int elo = static_cast<int>(vlo - x > 0 ? vlo - x : int64_t(0));
+            const int ehi = static_cast<int>(vhi - x < SO_S ? vhi - x : int64_t(SO_S));
+            uint32_t F[SO_SEGC];
+            const uint32_t cnt =
+                so_subtile<Word, Entry, HIST, WARM>(smem + wb * SO_BUF + SO_LHALO, tb, m, two, esz,
+                                                    carry, s == pend.sb && s > 0, elo, ehi, F);
+            uint32_t total;
+            const uint64_t idx = run + warp_excl_scan(cnt, &total);
+            so_write_flags(F, idx, cap, out, x - shift);
+            run += total;
             __syncwarp();
         }
+    };
+
+    while (t < a.total) {
+        const QueryDev &Q = query_of(a, qi);
+        so_table<Entry>(Q.plan, cur_plan, tbl, m);
         // Query fields in registers: the mbarrier waits are compiler
         // barriers, after which descriptor fields would be reloaded.
         const uint8_t *const qtext = Q.text;
@@ -374,15 +529,20 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
         const int64_t vlo = o + static_cast<int64_t>(m) - 1;  // first valid end
         const int64_t vhi = o + static_cast<int64_t>(qn);     // one past the last
         const int64_t ivstart = static_cast<int64_t>(sb) * SO_T;
+        uint32_t *hits = hits_base + hb * SO_HITS;
+        uint8_t *spill = spill_base ? spill_base + hb * SO_SPILL_ITEM : nullptr;
+        uint32_t *list = reinterpret_cast<uint32_t *>(spill);
+        uint8_t *flags = spill ? spill + SO_SPILL_POS * 4 : nullptr;
 
-        // ---- pass over the item's sub-tiles: count and buffer hits
+        // ---- pass over the item's sub-tiles: count and keep hits
         uint32_t count = 0;
         Word carry = 0;
         bool failed = false;
         int pending = 0;           // prefetches in flight when the loop stops early
-        bool spilling = false;     // later sub-tiles' flags go to the spill area
-        uint64_t spill_from = se;  // first spilled sub-tile
-        uint32_t buffered = 0;     // hits in the shared buffer when spilling began
+        int mode = 0;              // hits go to: 0 the shared buffer, 1 the list, 2 flag words
+        uint32_t buffered = 0;     // hits in the shared buffer when the list began
+        uint32_t listed = 0;       // hits in the list when the flag words began
+        uint64_t flag_from = se;   // first sub-tile kept as flag words
         for (uint64_t s = sb; s < se; ++s) {
             const int ahead = cur == 0 ? SO_NBUF - 1 : cur - 1;  // (cur + SO_NBUF - 1) mod SO_NBUF
             if (lane == 0 && s + SO_NBUF - 1 < se)
@@ -395,40 +555,34 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
                 for (int i = 1; i < SO_NBUF; ++i) pending += s + i < se;
                 break;
             }
-            const uint8_t *buf = smem + cur * SO_BUF + SO_LHALO;
-            const uint8_t *seg = buf + lane * SO_S;
-            uint32_t F[SO_SEGC];
-            if (WARM) {
-                so_local<Word, Entry, HIST>(seg, so_warmup<Word, Entry, WARM>(seg, tb, two, esz), tb, m,
-                                            two, esz, F);
-            } else {
-                if (s == sb && s > 0 && lane == 0) carry = so_warm<Word, Entry>(buf - (m - 1), tb, m, esz);
-                const Word Dend = so_local<Word, Entry, HIST>(seg, Word(0), tb, m, two, esz, F);
-                Word Dprev = __shfl_up_sync(0xffffffffu, Dend, 1);
-                if (lane == 0) Dprev = carry;
-                so_fixup<Word, Entry>(seg, tb, m, esz, Dprev, F);
-                carry = __shfl_sync(0xffffffffu, Dend, 31);
-            }
             const int64_t x = static_cast<int64_t>(s) * SO_T + lane * SO_S;
             // Only a text's first and last sub-tiles hold invalid ends.
             const bool edge = s == 0 || s + 1 == qnsub;
             const int elo = edge ? static_cast<int>(vlo - x > 0 ? vlo - x : int64_t(0)) : 0;
             const int ehi = edge ? static_cast<int>(vhi - x < SO_S ? vhi - x : int64_t(SO_S)) : SO_S;
-            const uint32_t cnt = so_mask_count(F, elo, ehi);
+            uint32_t F[SO_SEGC];
+            const uint32_t cnt = so_subtile<Word, Entry, HIST, WARM>(
+                smem + cur * SO_BUF + SO_LHALO, tb, m, two, esz, carry, s == sb && s > 0, elo, ehi, F);
             uint32_t total = 0, ex = 0;
             if (__any_sync(0xffffffffu, cnt != 0)) ex = warp_excl_scan(cnt, &total);
-            if (total != 0 && !spilling && count + total > SO_HITS && spill) {
-                spilling = true;
-                spill_from = s;
-                buffered = count;
+            if (total != 0 && spill) {
+                if (mode == 0 && count + total > SO_HITS) {
+                    mode = 1;
+                    buffered = count;
+                }
+                if (mode == 1 && count - buffered + total > SO_SPILL_POS) {
+                    mode = 2;
+                    listed = count - buffered;
+                    flag_from = s;
+                }
             }
-            if (spilling) {
+            if (mode == 2) {
                 // Keep this sub-tile's flags for the write phase.
-                uint16_t *dst = reinterpret_cast<uint16_t *>(spill + (s - sb) * SO_SUB_FLAGS);
+                uint16_t *dst = reinterpret_cast<uint16_t *>(flags + (s - flag_from) * SO_SUB_FLAGS);
 #pragma unroll
                 for (int c = 0; c < SO_SEGC; ++c) dst[c * 32 + lane] = static_cast<uint16_t>(F[c]);
-            } else if (cnt && count + total <= SO_HITS) {
-                uint32_t idx = count + ex;
+            } else if (cnt && (mode == 1 || count + total <= SO_HITS)) {
+                uint32_t *dst = mode == 0 ? hits + count + ex : list + (count - buffered) + ex;
                 const uint32_t rel0 = static_cast<uint32_t>(x - ivstart);
 #pragma unroll
                 for (int c = 0; c < SO_SEGC; ++c) {
@@ -436,7 +590,7 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
                     while (f) {
                         const int r = 31 - __clz(f);
                         f ^= 1u << r;
-                        hits[idx++] = rel0 + 16 * c + 15 - r;
+                        *dst++ = rel0 + 16 * c + 15 - r;
                     }
                 }
             }
@@ -446,10 +600,12 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
         }
         if (failed) {
             // The copy of sub-tile `cur` never completed; wait (bounded)
-            // for the prefetches still in flight, then leave.
+            // for the prefetches still in flight, then leave.  The pending
+            // item is marked failed too, so no successor waits for it.
             if (lane == 0) {
                 atomicOr(a.err, ERR_COPY);
                 st_relaxed(&Q.state[k], LB_ERR);
+                if (have_pending) st_relaxed(&query_of(a, pend.qi).state[pend.k], LB_ERR);
                 for (int i = 1; i <= pending; ++i) {
                     const int b = (cur + i) % SO_NBUF;
                     mbar_wait_bounded(&bar[b], (parity >> b) & 1u);
@@ -458,12 +614,12 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
             return;
         }
 
-        // ---- item prefix (decoupled look-back)
-        bool ok;
-        const uint64_t excl = lookback_exclusive(Q.state, k, count, a.err, &ok);
-        // Claim the next item only now: a warp never holds an unstarted item
-        // while it waits, so waits cannot cascade from query to query.  Its
-        // first sub-tile streams in while this item's hits are written.
+        // ---- publish this item's count; claim the next item and start its
+        // first sub-tiles; then finish the previous item.
+        lookback_publish(Q.state, k, count);
+        unsigned long long nt = a.total;
+        uint32_t nqi = 0;
+        uint64_t nk = 0;
         if (lane == 0 && so_claim(a, &nt, &nqi, &nk)) {
             const QueryDev &Qn = query_of(a, nqi);
             const uint64_t s0 = nk * Qn.sub_per_item;
@@ -476,94 +632,18 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
         nt = __shfl_sync(0xffffffffu, nt, 0);
         nqi = __shfl_sync(0xffffffffu, nqi, 0);
         nk = __shfl_sync(0xffffffffu, nk, 0);
-        if (ok && lane == 0 && k + 1 == Q.ntiles) *Q.out_count = excl + count;
-        const uint64_t cap = Q.cap;
-        uint64_t *out = Q.out_pos;
-        const int64_t shift = static_cast<int64_t>(m) - 1 + o;  // end -> real start
-        if (ok && (count <= SO_HITS || spilling)) {
-            const uint32_t nb = spilling ? buffered : count;
-            for (uint32_t r = lane; r < nb; r += 32) {
-                const uint64_t idx = excl + r;
-                if (idx < cap) out[idx] = static_cast<uint64_t>(ivstart + hits[r] - shift);
-            }
-            uint64_t run = excl + nb;
-            for (uint64_t s = spill_from; s < se && run < cap; ++s) {
-                const uint16_t *src = reinterpret_cast<const uint16_t *>(spill + (s - sb) * SO_SUB_FLAGS);
-                uint32_t F[SO_SEGC];
-                uint32_t cnt = 0;
-#pragma unroll
-                for (int c = 0; c < SO_SEGC; ++c) {
-                    F[c] = src[c * 32 + lane];
-                    cnt += __popc(F[c]);
-                }
-                uint32_t total;
-                uint64_t idx = run + warp_excl_scan(cnt, &total);
-                const int64_t x = static_cast<int64_t>(s) * SO_T + lane * SO_S;
-#pragma unroll
-                for (int c = 0; c < SO_SEGC; ++c) {
-                    uint32_t f = F[c];
-                    while (f) {
-                        const int r = 31 - __clz(f);
-                        f ^= 1u << r;
-                        if (idx < cap) out[idx] = static_cast<uint64_t>(x + 16 * c + 15 - r - shift);
-                        ++idx;
-                    }
-                }
-                run += total;
-            }
-        } else if (ok && excl < cap) {
-            // Too many hits to buffer: rescan the item in the free buffer and
-            // write each sub-tile's hits at their final offsets.
-            const int wb = cur == 0 ? SO_NBUF - 1 : cur - 1;  // the slot the next item leaves idle
-            uint64_t run = excl;
-            carry = 0;
-            for (uint64_t s = sb; s < se && run < cap; ++s) {
-                if (lane == 0) so_issue(smem + wb * SO_BUF, &bar[wb], qtext, qn, s);
-                const bool arrived = mbar_wait_bounded(&bar[wb], (parity >> wb) & 1u);
-                parity ^= 1u << wb;
-                if (!__all_sync(0xffffffffu, arrived)) {
-                    if (lane == 0) atomicOr(a.err, ERR_COPY);
-                    break;
-                }
-                const uint8_t *buf = smem + wb * SO_BUF + SO_LHALO;
-                const uint8_t *seg = buf + lane * SO_S;
-                uint32_t F[SO_SEGC];
-                if (WARM) {
-                    so_local<Word, Entry, HIST>(seg, so_warmup<Word, Entry, WARM>(seg, tb, two, esz), tb,
-                                                m, two, esz, F);
-                } else {
-                    if (s == sb && s > 0 && lane == 0) carry = so_warm<Word, Entry>(buf - (m - 1), tb, m, esz);
-                    const Word Dend = so_local<Word, Entry, HIST>(seg, Word(0), tb, m, two, esz, F);
-                    Word Dprev = __shfl_up_sync(0xffffffffu, Dend, 1);
-                    if (lane == 0) Dprev = carry;
-                    so_fixup<Word, Entry>(seg, tb, m, esz, Dprev, F);
-                    carry = __shfl_sync(0xffffffffu, Dend, 31);
-                }
-                const int64_t x = static_cast<int64_t>(s) * SO_T + lane * SO_S;
-                const int elo = static_cast<int>(vlo - x > 0 ? vlo - x : int64_t(0));
-                const int ehi = static_cast<int>(vhi - x < SO_S ? vhi - x : int64_t(SO_S));
-                const uint32_t cnt = so_mask_count(F, elo, ehi);
-                uint32_t total;
-                uint64_t idx = run + warp_excl_scan(cnt, &total);
-#pragma unroll
-                for (int c = 0; c < SO_SEGC; ++c) {
-                    uint32_t f = F[c];
-                    while (f) {
-                        const int r = 31 - __clz(f);
-                        f ^= 1u << r;
-                        if (idx < cap) out[idx] = static_cast<uint64_t>(x + 16 * c + 15 - r - shift);
-                        ++idx;
-                    }
-                }
-                run += total;
-                __syncwarp();
-            }
-        }
+        if (have_pending) write_pending();
+        if (mode == 0) buffered = count <= SO_HITS ? count : 0;
+        if (mode == 1) listed = count - buffered;
+        pend = SOItem{qi, k, sb, se, count, buffered, listed, flag_from};
+        have_pending = true;
+        hb ^= 1;
         __syncwarp();
         t = nt;
         qi = nqi;
         k = nk;
     }
+    if (have_pending) write_pending();
 }
 
 }  // namespace
@@ -697,7 +777,7 @@ extern "C" sm_status sm_search_noalloc(const uint8_t *text, uint64_t n, const ui
     const uint64_t o = reinterpret_cast<uintptr_t>(text) & 15u;
     const uint64_t units = (o + n + SO_T - 1) / SO_T;
     const uint64_t resident = static_cast<uint64_t>(d->sms) * static_cast<uint64_t>(d->bps[kid]);
-    uint64_t per = units / (4 * resident);
+    uint64_t per = (units + 4 * resident - 1) / (4 * resident);
     per = per < 1 ? 1 : (per > 64 ? 64 : per);
     const uint64_t items = (units + per - 1) / per;
     if (items > NA_MAX_ITEMS) return SM_EINVAL;  // cannot happen when n <= NA_MAX_N

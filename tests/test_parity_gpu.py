@@ -165,3 +165,22 @@ def test_device_generator_matches_host():
         smg.gen_text(out, 1000, spec.key, sigma, thr, bmap)
         smg.sync()
         assert np.array_equal(out.cpu().numpy(), spec.window(1000, spec.n - 1000))
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 4, 6, 9, 20])
+def test_long_work_items_hit_storage(m):
+    """Bit-parallel work items of many sub-tiles (config tile): hits kept in
+    shared memory, in the spill position list, and as spilled flag words
+    (densities 1/4 .. 1/4^9 on sigma = 4), bit-exact with the oracle."""
+    spec = gen.uniform_text((8 << 20) + 12_345, 4, seed=40 + m)
+    t = spec.host()
+    pats = gen.substring_patterns(t, m, 2, seed=m)
+    for off in (0, 7):
+        dev = to_dev(t, off)
+        for p in pats:
+            exp = oracle.naive_mt(t, p)
+            for wb in ((32, 64) if m <= 32 else (64,)):
+                for tile in (17, 22):
+                    got, total, _ = gpu_search(dev, p, "shiftor", 0, wb, tile=tile)
+                    assert total == len(exp), (off, wb, tile)
+                    assert np.array_equal(got, exp), (off, wb, tile)

@@ -244,7 +244,8 @@ def run_ours(args, world, rank, local):
         # this device before anything is timed.
         from paper_1012_2547_gb300 import tuner
         tr = tuner.tune(ms=tuple(int(x) for x in args.ms.split(",")) if args.ms else
-                        tuple(__import__("paper_1012_2547_gb300").gen.SWEEP_M))
+                        tuple(__import__("paper_1012_2547_gb300").gen.SWEEP_M),
+                        per=args.per_m or workloads.SWEEP_PER_M)
         tuning = {"seconds": tr["seconds"],
                   "choices": {f"s{r['sigma']}m{r['m']}": r["best"] for r in tr["report"]}}
 

@@ -360,19 +360,47 @@ __device__ __forceinline__ uint32_t so_subtile(const uint8_t *buf, uint32_t tb, 
     return so_mask_count(F, elo, ehi);
 }
 
-// Writes the flagged positions of a lane segment at out[idx...] (capped).
-__device__ __forceinline__ void so_write_flags(const uint32_t (&F)[SO_SEGC], uint64_t idx, uint64_t cap,
-                                               uint64_t *out, int64_t start0) {
+// Calls put(b) for every flagged byte b of a lane segment, b increasing.
+// F[c] bit r flags byte 16c + 15 - r; the 144 flags are first laid out in
+// byte order over two 64-bit words and one 32-bit word, so the lane loops
+// once per hit (not once per chunk holding one).
+static_assert(SO_SEGC == 9, "so_emit packs 9 chunks of flags");
+template <typename Put>
+__device__ __forceinline__ void so_emit(const uint32_t (&F)[SO_SEGC], Put put) {
+    uint32_t Q[5];
 #pragma unroll
-    for (int c = 0; c < SO_SEGC; ++c) {
-        uint32_t f = F[c];
-        while (f) {
-            const int r = 31 - __clz(f);
-            f ^= 1u << r;
-            if (idx < cap) out[idx] = static_cast<uint64_t>(start0 + 16 * c + 15 - r);
-            ++idx;
+    for (int w = 0; w < 5; ++w)
+        Q[w] = (__brev(F[2 * w]) >> 16) | (2 * w + 1 < SO_SEGC ? __brev(F[2 * w + 1]) : 0u);
+    uint64_t w0 = Q[0] | (static_cast<uint64_t>(Q[1]) << 32);
+    uint64_t w1 = Q[2] | (static_cast<uint64_t>(Q[3]) << 32);
+    uint32_t w2 = Q[4];
+    while (w0 | w1 | w2) {
+        uint32_t b;
+        if (w0) {
+            b = __ffsll(static_cast<long long>(w0)) - 1;
+            w0 &= w0 - 1;
+        } else if (w1) {
+            b = 63 + __ffsll(static_cast<long long>(w1));
+            w1 &= w1 - 1;
+        } else {
+            b = 127 + __ffs(w2);
+            w2 &= w2 - 1;
         }
+        put(b);
     }
+}
+
+// Writes the flagged positions of a lane segment at out[idx...] (capped):
+// idx0 + ex is the lane's first index, start0 the output value of sub-tile
+// position 0.
+__device__ __forceinline__ void so_write_flags(const uint32_t (&F)[SO_SEGC], uint32_t ex, uint64_t idx0,
+                                               uint64_t cap, uint64_t *out, int64_t start0) {
+    uint64_t idx = idx0 + ex;
+    const int64_t lane0 = start0 + static_cast<int64_t>(threadIdx.x & 31) * SO_S;
+    so_emit(F, [&](uint32_t b) {
+        if (idx < cap) out[idx] = static_cast<uint64_t>(lane0 + b);
+        ++idx;
+    });
 }
 
 // One warp per block.  The warp claims work items (query, item); an item
@@ -476,8 +504,8 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
                     cnt += __popc(F[c]);
                 }
                 uint32_t total;
-                const uint64_t idx = run + warp_excl_scan(cnt, &total);
-                so_write_flags(F, idx, cap, out, static_cast<int64_t>(s) * SO_T + lane * SO_S - shift);
+                const uint32_t ex = warp_excl_scan(cnt, &total);
+                so_write_flags(F, ex, run, cap, out, static_cast<int64_t>(s) * SO_T - shift);
                 run += total;
             }
             return;
@@ -508,8 +536,8 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
                 so_subtile<Word, Entry, HIST, WARM>(smem + wb * SO_BUF + SO_LHALO, tb, m, two, esz,
                                                     carry, s == pend.sb && s > 0, elo, ehi, F);
             uint32_t total;
-            const uint64_t idx = run + warp_excl_scan(cnt, &total);
-            so_write_flags(F, idx, cap, out, x - shift);
+            const uint32_t ex = warp_excl_scan(cnt, &total);
+            so_write_flags(F, ex, run, cap, out, static_cast<int64_t>(s) * SO_T - shift);
             run += total;
             __syncwarp();
         }
@@ -570,7 +598,9 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
                     mode = 1;
                     buffered = count;
                 }
-                if (mode == 1 && count - buffered + total > SO_SPILL_POS) {
+                // Flag words cost SO_SUB_FLAGS bytes a sub-tile, the list 4 a
+                // hit: a dense sub-tile, or a full list, switches to flags.
+                if (mode == 1 && (count - buffered + total > SO_SPILL_POS || 4 * total > SO_SUB_FLAGS)) {
                     mode = 2;
                     listed = count - buffered;
                     flag_from = s;
@@ -584,15 +614,7 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
             } else if (cnt && (mode == 1 || count + total <= SO_HITS)) {
                 uint32_t *dst = mode == 0 ? hits + count + ex : list + (count - buffered) + ex;
                 const uint32_t rel0 = static_cast<uint32_t>(x - ivstart);
-#pragma unroll
-                for (int c = 0; c < SO_SEGC; ++c) {
-                    uint32_t f = F[c];
-                    while (f) {
-                        const int r = 31 - __clz(f);
-                        f ^= 1u << r;
-                        *dst++ = rel0 + 16 * c + 15 - r;
-                    }
-                }
+                so_emit(F, [&](uint32_t b) { *dst++ = rel0 + b; });
             }
             count += total;
             __syncwarp();  // slot `cur` and the hit buffer are settled

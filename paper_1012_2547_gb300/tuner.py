@@ -81,11 +81,14 @@ def _time_batch(text, pats, sigma, cfg, reps, flush):
     return statistics.median(ts)
 
 
-def tune(sigmas=(2, 4, 8, 16, 32, 64, 128), ms=gen.SWEEP_M, n: int = 4 << 20, per: int = 16,
+def tune(sigmas=(2, 4, 8, 16, 32, 64, 128), ms=gen.SWEEP_M, n: int = 4 << 20, per: int = 100,
          reps: int = 3, seed: int = 101, apply: bool = True, verbose: bool = False) -> dict:
     """Measure every candidate for each (sigma, m) and return (and by
     default apply) the tuning table.  Cells not measured keep variant 0
-    (the library's built-in rule)."""
+    (the library's built-in rule).  `per` patterns per cell run as one
+    batch: the ranking of the kernels depends on the batch size (a small
+    batch gives short work items), so it should match the batches the
+    table will serve."""
     import torch
 
     from . import gen_text

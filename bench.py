@@ -305,6 +305,12 @@ def run_ours(args, world, rank, local):
             for b, (e0, e1) in zip(batches, ev):
                 b["times"].append(e0.elapsed_time(e1) / 1e3)
 
+    # The steps run inside an NVTX range, so a profiler can be limited to
+    # them (ncu --nvtx --nvtx-include bench_steps/) and skip the tuner's
+    # and the count pass's launches.
+    nvtx = getattr(torch.cuda, "nvtx", None)
+    if nvtx is not None:
+        nvtx.range_push("bench_steps")
     for _ in range(args.warmup):
         flush.zero_()
         step(False)
@@ -326,6 +332,8 @@ def run_ours(args, world, rank, local):
         step_times.append(sum(b["times"][-1] for b in batches))
     torch.cuda.synchronize()
     launches = smg.kernel_launches() - launches0
+    if nvtx is not None:
+        nvtx.range_pop()
     barrier(world)
     clk = clocks.stop()
     smg.sync()
@@ -448,12 +456,18 @@ def bench_bandwidth(args, world, rank, local):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     n = args.bw_bytes
-    w = workloads.bandwidth(n=n)
+    ms = tuple(int(x) for x in args.ms.split(",")) if args.ms else workloads.BANDWIDTH_M
+    w = workloads.bandwidth(n=n, per_m=args.per_m or 20, ms=ms)
+    tuning = None
+    if not args.no_tune:
+        from paper_1012_2547_gb300 import tuner
+        tr = tuner.tune(sigmas=(4,), ms=ms)
+        tuning = {"seconds": tr["seconds"], "choices": {f"s{r['sigma']}m{r['m']}": r["best"] for r in tr["report"]}}
     spec = w.specs[0]
     text = torch.empty(n, dtype=torch.uint8, device=dev)
     smg.gen_text(text, 0, spec.key, 4)
     # dense stress region: a^n-dominated first 64 MiB
-    dense = workloads.bandwidth_dense()
+    dense = workloads.bandwidth_dense(ms=ms)
     pre = min(workloads.DENSE_PREFIX, n)
     host_pre = spec.window(0, pre).copy()
     gen.plant_prefix(host_pre, pre, 4096, seed=77)
@@ -481,9 +495,176 @@ def bench_bandwidth(args, world, rank, local):
                 ts.append(e0.elapsed_time(e1) / 1e3)
         t = statistics.median(ts)
         res.append({"m": len(q.pattern), "n": nn, "hits": int(caps[i]), "ms": round(t * 1e3, 4),
-                    "GBs": round(nn / t / 1e9, 1), "variant": plans[i].info().variant})
+                    "GBs": round(nn / t / 1e9, 1), "variant": plans[i].info().variant,
+                    "kind": "dense" if q.n else ("substring" if i % (2 * (args.per_m or 20)) < (args.per_m or 20)
+                                                 else "random")})
     hbm, kind = peaks()
-    print(json.dumps({"workload": w.name, "peak_gbs": hbm, "peak_kind": kind, "results": res}))
+    for r in res:
+        r["frac"] = round(r["GBs"] / hbm, 4)
+    per_m = {}
+    for m in ms:
+        for k in ("substring", "random"):
+            g = [r["GBs"] for r in res if r["m"] == m and r["kind"] == k]
+            if g:
+                per_m.setdefault(str(m), {})[k + "_GBs"] = round(statistics.median(g), 1)
+        per_m[str(m)]["frac"] = round(min(per_m[str(m)].values()) / hbm, 4)
+    # Parity on samples: every hit the GPU reports inside a few windows of the
+    # text, and the count there, against the oracle on the host's copy of the
+    # window (regenerated from the seed).
+    import oracle
+    rng = np.random.default_rng(5)
+    checked, ok = 0, True
+    sample = sorted(set(rng.integers(0, len(w.queries), 6).tolist())) if n > workloads.DENSE_PREFIX + (4 << 20) else []
+    for i in sample:
+        q = w.queries[i]
+        m = len(q.pattern)
+        got_all = outs[i][:int(caps[i])]
+        for _ in range(3):
+            lo = int(rng.integers(workloads.DENSE_PREFIX, n - (1 << 20)))
+            hi = lo + (1 << 20)
+            win = spec.window(lo, hi - lo + m - 1)
+            exp = oracle.naive(win, q.pattern).astype(np.int64) + lo
+            a = int(torch.searchsorted(got_all, torch.tensor([lo], device=dev)).item())
+            b = int(torch.searchsorted(got_all, torch.tensor([hi], device=dev)).item())
+            got = got_all[a:b].cpu().numpy()
+            ok &= bool(np.array_equal(got, exp))
+            checked += 1
+    print(json.dumps({"workload": w.name, "metric": "scanned text GB/s (% of HBM peak) per sigma,m",
+                      "peak_gbs": hbm, "peak_kind": kind, "per_m": per_m,
+                      "parity_sample": {"windows": checked, "window_bytes": 1 << 20, "ok": ok},
+                      "tuning": tuning, "results": res}))
+
+
+# ---------------------------------------------------------------- batched workload
+
+def device_text(smg, spec, dev):
+    """A counter-based TextSpec built on the device by sm_gen_text."""
+    import numpy as np
+    import torch
+    t = torch.empty(spec.n, dtype=torch.uint8, device=dev)
+    if spec.kind == "uniform":
+        smg.gen_text(t, 0, spec.key, spec.sigma)
+    else:
+        thr = torch.tensor(np.asarray(spec.thresholds, dtype=np.uint32).view(np.int32), device=dev)
+        bm = torch.tensor(np.asarray(spec.byte_map, dtype=np.uint8), device=dev)
+        smg.gen_text(t, 0, spec.key, 0, thr, bm)
+    return t
+
+
+def bench_batched(args, world, rank, local):
+    """Batched queries: (i) 4096 patterns of log-uniform length on one shared
+    1 GiB sigma = 20 skewed text, (ii) 10,000 (pattern, text) pairs with
+    texts of 4 KiB .. 64 MiB over sigma 4 / 64.  Each part runs as one
+    graph-captured batch (one persistent launch per kernel family, kernels
+    picked by the autotuned table) and, for comparison, as one launch per
+    query (sm_search_plan on the same plans and outputs).  L2 is flushed
+    before each timed pass.  Reports queries/s and scanned GB/s of both."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    import paper_1012_2547_gb300 as smg
+    from paper_1012_2547_gb300 import workloads
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    tuning = None
+    if not args.no_tune:
+        from paper_1012_2547_gb300 import tuner
+        tr = tuner.tune(sigmas=(4, 16, 64))
+        tuning = {"seconds": tr["seconds"]}
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    rng = np.random.default_rng(3)
+    parts = {}
+    for name, w in (("shared_1GiB_sigma20_q4096", workloads.batched_shared()),
+                    ("pairs_10000_4KiB-64MiB_sigma4-64", workloads.batched_pairs())):
+        base = [device_text(smg, sp, dev) for sp in w.specs]
+        texts = [base[q.text_id][q.offset:q.offset + (q.n or w.specs[q.text_id].n)] for q in w.queries]
+        smg.sync()
+        nq = len(w.queries)
+        plans = [None] * nq
+        by_sigma = {}
+        for i, q in enumerate(w.queries):
+            by_sigma.setdefault(q.sigma_hint, []).append(i)
+        for sg, idx in by_sigma.items():
+            for i, p in zip(idx, smg.prepare_many([w.queries[i].pattern for i in idx], sigma_hint=sg)):
+                plans[i] = p
+        cnt = torch.zeros(nq, dtype=torch.int64, device=dev)
+        smg.search_batch([(texts[i], plans[i], None, cnt[i:i + 1]) for i in range(nq)])
+        smg.sync()
+        c = cnt.cpu().numpy()
+        offs = np.concatenate([[0], np.cumsum(c)])
+        out = torch.empty(max(int(c.sum()), 1), dtype=torch.int64, device=dev)
+        items = [(texts[i], plans[i], out[int(offs[i]):int(offs[i + 1])], cnt[i:i + 1]) for i in range(nq)]
+        batch = smg.Batch(items, graph=True)
+        scanned = sum(t.numel() for t in texts)
+
+        def timed(fn, reps):
+            ts = []
+            for r in range(args.warmup + reps):
+                flush.zero_()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if r >= args.warmup:
+                    ts.append(e0.elapsed_time(e1) / 1e3)
+            return statistics.median(ts)
+
+        l0 = smg.kernel_launches()
+        tb = timed(lambda: batch.launch(stream), args.steps)
+        launches_b = (smg.kernel_launches() - l0) // (args.warmup + args.steps)
+
+        def per_query():
+            for i in range(nq):
+                smg.search_into(texts[i], plans[i], items[i][2], cnt[i:i + 1], cap=int(c[i]))
+        l0 = smg.kernel_launches()
+        tq = timed(per_query, max(1, min(args.steps, 3)))
+        launches_q = (smg.kernel_launches() - l0) // (args.warmup + max(1, min(args.steps, 3)))
+        smg.sync()
+        # parity: a sample of queries against the oracle (whole text when it
+        # is small, else every hit in a few 1 MiB windows)
+        ok, checked = True, 0
+        for i in sorted(set(rng.integers(0, nq, 8).tolist())):
+            q = w.queries[i]
+            spec = w.specs[q.text_id]
+            n = q.n or spec.n
+            got = out[int(offs[i]):int(offs[i + 1])]
+            m = len(q.pattern)
+            if n <= (8 << 20):
+                exp = oracle.naive(spec.window(q.offset, n), q.pattern)
+                ok &= int(cnt[i].item()) == len(exp) and bool(np.array_equal(got.cpu().numpy().astype(np.uint64), exp))
+            else:
+                for _ in range(2):
+                    lo = int(rng.integers(0, n - (1 << 20)))
+                    exp = oracle.naive(spec.window(q.offset + lo, (1 << 20) + m - 1), q.pattern).astype(np.int64) + lo
+                    a = int(torch.searchsorted(got, torch.tensor([lo], device=dev)).item())
+                    b = int(torch.searchsorted(got, torch.tensor([lo + (1 << 20)], device=dev)).item())
+                    ok &= bool(np.array_equal(got[a:b].cpu().numpy(), exp))
+            checked += 1
+        parts[name] = {
+            "queries": nq, "scanned_bytes": scanned, "positions": int(c.sum()),
+            "batched": {"ms": round(tb * 1e3, 3), "queries_per_s": round(nq / tb, 1),
+                        "scanned_GBs": round(scanned / tb / 1e9, 1), "launches": int(launches_b)},
+            "per_query": {"ms": round(tq * 1e3, 3), "queries_per_s": round(nq / tq, 1),
+                          "scanned_GBs": round(scanned / tq / 1e9, 1), "launches": int(launches_q)},
+            "speedup": round(tq / tb, 2),
+            "parity_sample": {"queries": checked, "ok": ok},
+        }
+        batch.free()
+        for p in plans:
+            p.free()
+        del out, texts, base, items, batch
+        torch.cuda.empty_cache()
+    hbm, kind = peaks()
+    print(json.dumps({"workload": "batched", "metric": "queries/s and scanned GB/s, batched vs one launch per query",
+                      "peak_gbs": hbm, "peak_kind": kind, "l2": "flushed (256 MiB write) before each pass",
+                      "tuning": tuning, "parts": parts}))
 
 
 # ---------------------------------------------------------------- serving workload
@@ -648,7 +829,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["sweep", "single", "bandwidth", "serve"], default="sweep")
+    ap.add_argument("--workload", choices=["sweep", "single", "bandwidth", "batched", "serve"], default="sweep")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -684,6 +865,10 @@ def main():
         if args.workload == "serve":
             if rank == 0:
                 bench_serve(args, world, rank, local)
+            return
+        if args.workload == "batched":
+            if rank == 0:
+                bench_batched(args, world, rank, local)
             return
         out = run_ours(args, world, rank, local)
         if rank == 0:

@@ -44,6 +44,8 @@ STREAM_OFFSETS = 2
 STREAM_RANDPAT = 3
 STREAM_MARKOV_ROWS = 4
 STREAM_PLANT = 5
+STREAM_LENGTHS = 6
+STREAM_SIZES = 7
 
 
 def mix64_int(z: int) -> int:

@@ -10,6 +10,12 @@ Input construction only (texts, patterns, sizes); no matching arithmetic.
   bandwidth : one 8 GiB uniform sigma = 4 text built on the device,
               m in {4, 32, 256, 1024}, 20 substring + 20 random patterns per
               m, and a^m on an a^n-dominated 64 MiB prefix.
+  batched   : (i) 4096 patterns, m log-uniform in [2, 1024], half
+              substrings and half i.i.d. uniform over the 20 symbols, on one
+              shared 1 GiB protein-like (sigma = 20, skewed) text; (ii) 10,000
+              (pattern, text) pairs, text lengths log-uniform in [4 KiB,
+              64 MiB], sigma alternating 4 / 64, m log-uniform in [2, 1024],
+              substring patterns.  Device-built texts.
 """
 from __future__ import annotations
 
@@ -29,6 +35,7 @@ class Query:
     pattern: bytes
     sigma_hint: int
     n: int | None = None  # None = the whole text
+    offset: int = 0       # first byte of the query's text within texts[text_id]
 
 
 @dataclass
@@ -90,3 +97,53 @@ def bandwidth(n: int = BANDWIDTH_N, per_m: int = 20, ms=BANDWIDTH_M, seed: int =
 
 def bandwidth_dense(ms=BANDWIDTH_M, prefix: int = DENSE_PREFIX) -> list[Query]:
     return [Query(0, bytes(m), 4, n=prefix) for m in ms]
+
+
+BATCHED_SHARED_N = 1 << 30
+BATCHED_SHARED_Q = 4096
+BATCHED_PAIRS = 10_000
+
+
+def batched_shared(n: int = BATCHED_SHARED_N, nq: int = BATCHED_SHARED_Q, seed: int = 31) -> Workload:
+    """One shared protein-like text (device-built; texts[0] is its TextSpec)
+    and nq patterns of length floor(2 * 512**u), u uniform: even queries are
+    substrings at seeded offsets, odd ones i.i.d. uniform over the 20
+    symbols."""
+    spec = gen.protein_text(n, seed)
+    w = Workload(f"batched_shared_n{n}_sigma20_q{nq}", [spec], [spec])
+    klen = gen.stream_key(seed, gen.STREAM_LENGTHS)
+    alphabet = np.arange(20, dtype=np.uint8)
+    for i in range(nq):
+        m = gen.log_uniform_int(klen, i, 2, 1024)
+        if i % 2 == 0:
+            o = gen.pattern_offsets(n, m, 1, seed=seed * 1_000_003 + i)[0]
+            p = bytes(spec.window(o, m))
+        else:
+            p = gen.random_patterns(alphabet, m, 1, seed=seed * 1_000_003 + i)[0]
+        w.queries.append(Query(0, p, 20))
+    return w
+
+
+def batched_pairs(count: int = BATCHED_PAIRS, seed: int = 41, lo: int = 4096,
+                  hi: int = 64 << 20) -> Workload:
+    """count (pattern, text) pairs.  Pair i has its own text of
+    floor(lo * (hi/lo)**u) bytes over sigma 4 (even i) or 64 (odd i): a
+    disjoint slice of one long device-built text per sigma (texts[0] for
+    sigma 4, texts[1] for 64), and a substring pattern of length
+    floor(2 * 512**u') at a seeded offset inside it."""
+    ksz = gen.stream_key(seed, gen.STREAM_SIZES)
+    klen = gen.stream_key(seed, gen.STREAM_LENGTHS)
+    sizes = [gen.log_uniform_int(ksz, i, lo, hi) for i in range(count)]
+    total = [0, 0]
+    offs = []
+    for i, n in enumerate(sizes):
+        offs.append(total[i % 2])
+        total[i % 2] += n
+    specs = [gen.uniform_text(total[0], 4, seed + 4), gen.uniform_text(total[1], 64, seed + 64)]
+    w = Workload(f"batched_pairs_{count}_n{lo}-{hi}_sigma4-64", specs, specs)
+    for i, n in enumerate(sizes):
+        spec = specs[i % 2]
+        m = min(gen.log_uniform_int(klen, i, 2, 1024), n)
+        o = gen.pattern_offsets(n, m, 1, seed=seed * 1_000_003 + i)[0]
+        w.queries.append(Query(i % 2, bytes(spec.window(offs[i] + o, m)), spec.sigma, n=n, offset=offs[i]))
+    return w

@@ -32,6 +32,7 @@ is the max over ranks.
 from __future__ import annotations
 
 import argparse
+import functools
 import hashlib
 import json
 import os
@@ -723,8 +724,20 @@ def bench_serve(args, world, rank, local):
     def run_server(arrival_rate=None):
         srv = Server(corp, budget_bytes=args.serve_budget, streams=4, max_batch=512,
                      sigma_hints=hints)
+        # Each result is consumed when it is ready, as the clients of a
+        # service would (a callback keeps its length and lets it go), so
+        # finished results do not pile up behind slower ones.
+        lens = [None] * len(reqs)
+        cond = threading.Condition()
+        ndone = [0]
+
+        def consume(f, k):
+            lens[k] = len(f.result())
+            with cond:
+                ndone[0] += 1
+                cond.notify()
+
         t0 = time.perf_counter()
-        futs = []
         if arrival_rate:
             # Poisson arrivals: every request whose scheduled arrival has
             # passed is submitted with that time as its arrival (so any lag
@@ -735,19 +748,17 @@ def bench_serve(args, world, rank, local):
                 now = time.perf_counter()
                 while k < len(reqs) and arrive[k] <= now:
                     pat, name, own = reqs[k]
-                    futs.append(srv.submit(pat, corpus=name, text=own, t_arrival=float(arrive[k])))
+                    srv.submit(pat, corpus=name, text=own, t_arrival=float(arrive[k])).add_done_callback(
+                        functools.partial(consume, k=k))
                     k += 1
                 if k < len(reqs):
                     time.sleep(min(max(arrive[k] - time.perf_counter(), 0.0), 0.001))
         else:
-            for pat, name, own in reqs:
-                futs.append(srv.submit(pat, corpus=name, text=own))
-        # Consume results as a client would: keep each result's length and
-        # drop the array, so the pinned copy-back buffers are recycled.
-        lens = []
-        for k in range(len(futs)):
-            lens.append(len(futs[k].result()))
-            futs[k] = None
+            for k, (pat, name, own) in enumerate(reqs):
+                srv.submit(pat, corpus=name, text=own).add_done_callback(functools.partial(consume, k=k))
+        with cond:
+            while ndone[0] < len(reqs):
+                cond.wait(60.0)
         dt = time.perf_counter() - t0
         srv.close()
         st = srv.stats()
@@ -774,12 +785,14 @@ def bench_serve(args, world, rank, local):
         st, _ = run_server(arrival_rate=frac * sat["qps"])
         loads[str(frac)] = {"offered_qps": round(frac * sat["qps"], 1), "qps": st["qps"],
                             "p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
-                            "batches": st["batches"], "host_s": st["host_s"]}
+                            "batches": st["batches"], "host_s": st["host_s"],
+                            "pinned_pool_bytes": st["pinned_pool_bytes"]}
     out = {
         "workload": f"serve_{len(reqs)}q_corpus{C}", "metric": "served queries/s, p50/p99 latency",
         "queries": len(reqs), "scanned_bytes": scanned,
         "batched": {"qps": sat["qps"], "scanned_GBs": round(scanned / sat["seconds"] / 1e9, 1),
                     "batches": sat["batches"], "retries": sat["retries"], "host_s": sat["host_s"],
+                    "pinned_pool_bytes": sat["pinned_pool_bytes"],
                     "seconds": sat["seconds"]},
         "unbatched": {"qps": round(len(reqs) / unb_dt, 1),
                       "p50_ms": round(float(np.percentile(lat1, 50)) * 1e3, 3),
@@ -840,7 +853,7 @@ def main():
     ap.add_argument("--ms", default="", help="sweep subset: comma-separated pattern lengths")
     ap.add_argument("--per-m", type=int, default=0, help="sweep subset: patterns per (text, m)")
     ap.add_argument("--serve-queries", type=int, default=4000)
-    ap.add_argument("--serve-corpus", type=int, default=256 << 20)
+    ap.add_argument("--serve-corpus", type=int, default=2 << 30)
     ap.add_argument("--serve-budget", type=int, default=40 << 30)
     ap.add_argument("--serve-loads", type=float, nargs="*", default=[0.5, 0.8, 0.95])
     ap.add_argument("--serve-no-unbatched", action="store_true")

@@ -17,7 +17,9 @@ thread repeatedly
      (one persistent launch per kernel family, in memory the server owns),
      followed by the copy of the counts and an event; once the counts are
      on the host, exactly the valid positions of each request are copied
-     back (a second event).
+     back (a second event): small results through a per-stream pinned
+     staging buffer, large ones straight into a pinned block of their own
+     that the client receives without a copy (``PinnedPool``).
 
 Up to ``streams`` batches are in flight at once, so requests that arrive
 while others run are admitted as slots and memory free up and their work
@@ -29,9 +31,11 @@ from __future__ import annotations
 
 import collections
 import concurrent.futures as cf
+import ctypes
 import itertools
 import threading
 import time
+import weakref
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -131,13 +135,84 @@ class Policy:
         self.used -= nbytes
 
 
+class PinnedPool:
+    """Pinned host blocks for large results, recycled when the result they
+    back is freed.  Block sizes are 1, 1.25, 1.5 or 1.75 times a power of
+    two (at least 1 MiB), so a block wastes under a fifth of its bytes; a
+    result is handed out as a numpy array over its block, and a
+    finalizer puts the block back on its free list once that array and every
+    view of it are gone, so steady-state serving allocates no pinned
+    memory."""
+
+    MIN_BYTES = 1 << 20
+
+    def __init__(self, torch, max_bytes: int = 4 << 30):
+        self._torch = torch
+        self._free = collections.defaultdict(list)
+        self._lock = threading.Lock()
+        self.allocated_bytes = 0
+        self.max_bytes = int(max_bytes)
+
+    @classmethod
+    def size_class(cls, nbytes: int) -> int:
+        """Smallest block size (k/4 * 2**e, k in 4..7) holding nbytes."""
+        n = max(int(nbytes), cls.MIN_BYTES)
+        e = (n - 1).bit_length() - 1          # 2**e < n <= 2**(e+1)
+        for k in (5, 6, 7, 8):
+            if (k << e) >> 2 >= n:
+                return (k << e) >> 2
+        return 1 << (e + 1)
+
+    def take(self, nbytes: int):
+        """A free block of at least nbytes (the smallest one up to twice the
+        size class), else a new block of the size class, else (the pool is
+        at max_bytes) (None, 0)."""
+        size = self.size_class(nbytes)
+        with self._lock:
+            fits = [c for c, blocks in self._free.items() if blocks and size <= c <= 2 * size]
+            if fits:
+                c = min(fits)
+                return self._free[c].pop(), c
+            if self.allocated_bytes + size > self.max_bytes:
+                return None, 0
+            self.allocated_bytes += size
+        return self._torch.empty(size, dtype=self._torch.uint8, pin_memory=True), size
+
+    def _give(self, block, cls: int) -> None:
+        with self._lock:
+            self._free[cls].append(block)
+
+    _shared = None
+
+    @classmethod
+    def shared(cls, torch, max_bytes: int):
+        """The process-wide pool (servers of one process share warm blocks),
+        allowed at least max_bytes."""
+        if cls._shared is None:
+            cls._shared = cls(torch, max_bytes)
+        cls._shared.max_bytes = max(cls._shared.max_bytes, int(max_bytes))
+        return cls._shared
+
+    def view(self, block, cls: int, count: int) -> np.ndarray:
+        """The first `count` 64-bit values of `block` as a uint64 array.
+        The array is made over a ctypes buffer, which every numpy view of it
+        references (numpy collapses view chains to the buffer's owner); the
+        finalizer on that buffer keeps the block until the last view is
+        gone, then returns it to the pool."""
+        buf = (ctypes.c_uint64 * max(count, 1)).from_address(block.data_ptr())
+        weakref.finalize(buf, self._give, block, cls)
+        return np.frombuffer(buf, dtype=np.uint64, count=count)
+
+
 class Server:
     """Continuous-batching exact-match server on one GPU (see module doc)."""
+
+    SMALL_RESULT = 8192  # positions; larger results get a pinned block of their own
 
     def __init__(self, corpora: dict, budget_bytes: int = 40 << 30, streams: int = 4,
                  max_batch: int = 512, max_wait: float = 0.0005, first_cap: int = 256,
                  sigma_hints: dict | None = None, own_text_sigma: int = 0,
-                 staging_bytes: int = 256 << 20):
+                 staging_bytes: int = 256 << 20, pinned_pool_bytes: int | None = None):
         import torch
 
         import paper_1012_2547_gb300 as smg
@@ -148,15 +223,21 @@ class Server:
         self.own_text_sigma = own_text_sigma
         self.first_cap = int(first_cap)
         self.policy = Policy(budget_bytes, max_batch, max_wait,
-                             {k: v.numel() for k, v in self.corpora.items()},
-                             max_batch_out_bytes=staging_bytes)
+                             {k: v.numel() for k, v in self.corpora.items()})
         self.streams = [torch.cuda.Stream() for _ in range(streams)]
         self.inflight: list[dict | None] = [None] * streams
-        # Per-stream pinned staging for copy-back, allocated up front: a
-        # batch's outputs fit it (Policy caps them), except a single larger
-        # request, for which it grows once.
-        self._staging: list = [torch.empty(max(staging_bytes // 8, 1), dtype=torch.int64, pin_memory=True)
+        # Per-stream pinned staging for the copy-back of small results
+        # (at most max_batch * SMALL_RESULT positions a batch), allocated up
+        # front; large results use blocks of the pool.
+        staging = max(staging_bytes // 8, max_batch * self.SMALL_RESULT)
+        self._staging: list = [torch.empty(staging, dtype=torch.int64, pin_memory=True)
                                for _ in range(streams)]
+        # Results in flight are bounded by the device budget (their device
+        # buffers fit it), so the pinned pool gets the budget plus slack for
+        # its size classes; a result that finds it full is copied to
+        # ordinary host memory instead.
+        self.pool = PinnedPool.shared(torch, budget_bytes + (8 << 30) if pinned_pool_bytes is None
+                                      else pinned_pool_bytes)
         self.latencies: list[float] = []
         self.completed = 0
         self.retries = 0
@@ -213,6 +294,7 @@ class Server:
     def stats(self) -> dict:
         lat = np.array(self.latencies) if self.latencies else np.zeros(1)
         return {"completed": self.completed, "batches": self.batches, "retries": self.retries,
+                "pinned_pool_bytes": self.pool.allocated_bytes,
                 "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
                 "host_s": {k: round(v, 4) for k, v in self.host_s.items()}}
 
@@ -293,26 +375,35 @@ class Server:
 
     def _copy_back(self, i: int, rec: dict) -> None:
         """Counts are on the host: copy back exactly the valid positions of
-        each complete request (not the whole capacity), then an event."""
+        each complete request (not the whole capacity), then an event.
+        Small results go through the stream's staging buffer, large ones
+        into a pinned block of their own."""
         torch = self._torch
         counts = rec["cnt_h"].numpy()
         caps = np.array([r.cap for r in rec["batch"]], dtype=np.int64)
         take = np.where(counts <= caps, counts, 0)
-        dst_offs = np.concatenate([[0], np.cumsum(take)])
-        need = max(int(dst_offs[-1]), 1)
-        if self._staging[i] is None or self._staging[i].numel() < need:
-            self._staging[i] = torch.empty(max(need + need // 4, 1 << 20), dtype=torch.int64,
-                                           pin_memory=True)
+        small = np.where(take < self.SMALL_RESULT, take, 0)
+        dst_offs = np.concatenate([[0], np.cumsum(small)])
         out_h = self._staging[i]
         out = rec["keep"][2]
+        blocks = {}
         s = self.streams[i]
         with torch.cuda.stream(s):
             for j in np.flatnonzero(take):
                 a = int(rec["offs"][j])
-                out_h[int(dst_offs[j]):int(dst_offs[j + 1])].copy_(out[a:a + int(take[j])], non_blocking=True)
+                c = int(take[j])
+                if c < self.SMALL_RESULT:
+                    out_h[int(dst_offs[j]):int(dst_offs[j + 1])].copy_(out[a:a + c], non_blocking=True)
+                else:
+                    block, cls = self.pool.take(8 * c)
+                    if block is None:  # pool full: an ordinary host array (a blocking copy)
+                        blocks[j] = out[a:a + c].cpu().numpy().view(np.uint64)
+                        continue
+                    block[: 8 * c].view(torch.int64).copy_(out[a:a + c], non_blocking=True)
+                    blocks[j] = (block, cls)
             ev = torch.cuda.Event()
             ev.record(s)
-        rec.update(out_h=out_h, dst_offs=dst_offs, event=ev, phase=1)
+        rec.update(out_h=out_h, dst_offs=dst_offs, blocks=blocks, event=ev, phase=1)
 
     def _retire(self) -> bool:
         done_any = False
@@ -337,11 +428,12 @@ class Server:
                     r.attempts += 1
                     requeue.append(r)
                     continue
-                # Copied out of the stream's reusable pinned staging buffer
-                # (torch's CPU copy runs on several threads).
-                res = self._torch.empty(c, dtype=self._torch.int64)
-                res.copy_(rec["out_h"][int(offs[j]):int(offs[j]) + c])
-                pos = res.numpy().view(np.uint64)
+                if j in rec["blocks"]:
+                    b = rec["blocks"][j]
+                    pos = b if isinstance(b, np.ndarray) else self.pool.view(*b, c)  # no copy
+                else:
+                    # out of the stream's reusable staging buffer
+                    pos = out_h[int(offs[j]):int(offs[j]) + c].astype(np.uint64)
                 self.latencies.append(now - r.t_arrival)
                 self.completed += 1
                 r.future.set_result(pos)

@@ -63,6 +63,14 @@ def test_batch_output_cap():
     assert [r.rid for r in b3] == [3]                        # alone, though above the cap
 
 
+def test_pinned_pool_size_classes():
+    from paper_1012_2547_gb300.serve import PinnedPool
+    for n in (1, 1 << 20, (1 << 20) + 1, 1_300_000, 3 << 20, (8 << 20) + 5, 1 << 31):
+        c = PinnedPool.size_class(n)
+        assert c >= n and c >= PinnedPool.MIN_BYTES
+        assert c <= 1.25 * max(n, PinnedPool.MIN_BYTES) + 1     # under a fifth wasted
+
+
 def test_ready_rules():
     p = Policy(budget_bytes=1 << 30, max_batch=2, max_wait=0.01)
     assert not p.ready(0.0, busy=0)
@@ -114,3 +122,27 @@ def test_server_results_equal_alone_and_in_mix():
         alone = smg.search(dev[name] if name else torch.from_numpy(own).cuda(), p).cpu().numpy().astype(np.uint64)
         assert np.array_equal(got, alone)
         assert np.array_equal(got, oracle.kmp(host, p))
+
+
+@pytest.mark.gpu
+def test_pinned_pool_recycles_blocks():
+    """A large result is a view of a pooled pinned block; the block goes
+    back to the pool when the result is freed, and is then reused."""
+    import gc
+
+    import torch
+
+    from paper_1012_2547_gb300.serve import PinnedPool
+    pool = PinnedPool(torch)
+    b, c = pool.take(3 << 20)
+    b[: 8 * 5].view(torch.int64).copy_(torch.arange(5))
+    a = pool.view(b, c, 5)
+    assert a.dtype == np.uint64 and a.tolist() == [0, 1, 2, 3, 4]
+    del b
+    gc.collect()
+    assert not pool._free[c]                                  # still backing `a`
+    del a
+    gc.collect()
+    assert len(pool._free[c]) == 1
+    b2, c2 = pool.take(3 << 20)
+    assert c2 == c and pool.allocated_bytes == c             # reused, not reallocated

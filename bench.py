@@ -371,13 +371,16 @@ def run_ours(args, world, rank, local):
                                                       "ms": round(statistics.mean(b["times"]) * 1e3, 4)}
                              for b in batches}}
 
-    # e2e through the C ABI from pinned host buffers
+    # e2e through the C ABI from pinned host buffers: texts H2D, plans built
+    # and uploaded (sm_prepare_many), the batch described by pointer arrays
+    # (query_array) and run (sm_search_batch), positions and counts D2H.
     e2e = None
     if not args.no_e2e:
         pinned = [torch.from_numpy(t).pin_memory() for t in texts_h]
         outs_h = torch.empty(max(total_hits, 1), dtype=torch.int64).pin_memory()
         cnts_h = torch.empty(nq, dtype=torch.int64).pin_memory()
         h2d = sum(len(t) for t in texts_h)
+        text_ids = np.array([q.text_id for q in queries], dtype=np.int64)
         e2e_times = []
         plan_bytes = 0
         for r in range(max(1, args.e2e_steps) + 1):
@@ -390,9 +393,13 @@ def run_ours(args, world, rank, local):
                 ps = smg.prepare_many([queries[i].pattern for i in idx], sigma_hint=sg)
                 for i, p in zip(idx, ps):
                     pl[i] = p
-            its = [(texts_d[q.text_id], pl[i], outbuf[int(offs[i]):int(offs[i + 1])], counts[i:i + 1])
-                   for i, q in enumerate(queries)]
-            smg.search_batch(its)
+            base = np.array([t.data_ptr() for t in texts_d], dtype=np.uint64)
+            lens = np.array([t.numel() for t in texts_d], dtype=np.uint64)
+            qarr = smg.query_array(base[text_ids], lens[text_ids], pl,
+                                   np.uint64(outbuf.data_ptr()) + 8 * offs[:-1].astype(np.uint64),
+                                   cnt_h.astype(np.uint64),
+                                   np.uint64(counts.data_ptr()) + 8 * np.arange(nq, dtype=np.uint64))
+            smg.search_batch_array(qarr)
             outs_h.copy_(outbuf, non_blocking=True)
             cnts_h.copy_(counts, non_blocking=True)
             torch.cuda.synchronize()

@@ -256,6 +256,14 @@ def batch_workspace_size_array(qarr) -> int:
     return int(out.value)
 
 
+def search_batch_array(qarr, stream=None) -> None:
+    """sm_search_batch on an array from query_array (library workspace)."""
+    if len(qarr) == 0:
+        return
+    ptr = ctypes.cast(qarr.ctypes.data, ctypes.POINTER(sm_query))
+    check(_lib.load().sm_search_batch(ptr, len(qarr), _stream_ptr(stream)), "sm_search_batch")
+
+
 def search_batch(items, stream=None) -> None:
     """sm_search_batch over (text, plan, out_pos, out_count[, n]) tuples."""
     if not items:

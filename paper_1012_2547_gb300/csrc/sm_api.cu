@@ -304,21 +304,19 @@ sm_status build_blob(const uint8_t *p, uint32_t m, uint32_t sigma, const sm_conf
         return SM_EINVAL;
     }
 
-    // q-gram table: keys in first-seen order, offsets per key descending.
-    std::vector<uint64_t> keys;
-    std::unordered_map<uint64_t, std::vector<uint32_t>> groups;
+    // q-gram table: (packed q-gram, offset) pairs sorted by q-gram, then by
+    // offset descending, so each distinct q-gram is one run of its offsets
+    // in the order the kernel emits candidates.
+    std::vector<std::pair<uint64_t, uint32_t>> grams;
+    uint32_t nkeys = 0;
     if (h.variant == VAR_QGRAM) {
-        for (uint32_t j = 0; j + q <= m; ++j) {
-            const uint64_t g = pack_qgram(p + j, q);
-            auto it = groups.find(g);
-            if (it == groups.end()) {
-                keys.push_back(g);
-                groups[g].push_back(j);
-            } else {
-                it->second.push_back(j);
-            }
-        }
-        h.slot_bits = std::max(4u, ceil_log2(2ull * keys.size()));
+        grams.reserve(m - q + 1);
+        for (uint32_t j = 0; j + q <= m; ++j) grams.emplace_back(pack_qgram(p + j, q), j);
+        std::sort(grams.begin(), grams.end(), [](const auto &x, const auto &y) {
+            return x.first != y.first ? x.first < y.first : x.second > y.second;
+        });
+        for (size_t i = 0; i < grams.size(); ++i) nkeys += i == 0 || grams[i].first != grams[i - 1].first;
+        h.slot_bits = std::max(4u, ceil_log2(2ull * nkeys));
         h.bm_bits = std::min(16u, std::max(10u, h.slot_bits + 4));
     }
 
@@ -351,12 +349,10 @@ sm_status build_blob(const uint8_t *p, uint32_t m, uint32_t sigma, const sm_conf
         // esz bytes (the kernel supplies the ones above them); stored
         // little-endian, as the device reads them.
         const uint64_t low = m >= 64 ? ~0ull : ((1ull << m) - 1);
-        for (int c = 0; c < 256; ++c) {
-            uint64_t w = ~low;
-            for (uint32_t j = 0; j < m; ++j)
-                if (p[j] == c) w |= 1ull << j;
-            std::memcpy(b + h.off_tbl + esz * c, &w, esz);
-        }
+        uint64_t B[256];
+        for (int c = 0; c < 256; ++c) B[c] = ~low;
+        for (uint32_t j = 0; j < m; ++j) B[p[j]] |= 1ull << j;
+        for (int c = 0; c < 256; ++c) std::memcpy(b + h.off_tbl + esz * c, &B[c], esz);
     }
     std::memcpy(b + h.off_pat, p, m);
     if (h.variant == VAR_QGRAM) {
@@ -364,18 +360,20 @@ sm_status build_blob(const uint8_t *p, uint32_t m, uint32_t sigma, const sm_conf
         QSlot *slots = reinterpret_cast<QSlot *>(b + h.off_slots);
         uint32_t *offs = reinterpret_cast<uint32_t *>(b + h.off_offs);
         const uint32_t mask = (1u << h.slot_bits) - 1;
-        uint32_t next = 0;
-        for (uint64_t g : keys) {
-            const std::vector<uint32_t> &js = groups[g];
+        for (size_t i = 0; i < grams.size();) {
+            const uint64_t g = grams[i].first;
+            size_t e = i;
+            while (e < grams.size() && grams[e].first == g) ++e;
             const uint64_t hh = g * 0x9E3779B97F4A7C15ull;
             const uint32_t bb = static_cast<uint32_t>(hh >> (64 - h.bm_bits));
             bitmap[bb >> 5] |= 1u << (bb & 31);
             uint32_t sl = static_cast<uint32_t>(hh >> (64 - h.slot_bits));
             while (slots[sl].count) sl = (sl + 1) & mask;
             slots[sl].key = g;
-            slots[sl].first = next;
-            slots[sl].count = static_cast<uint32_t>(js.size());
-            for (size_t r = js.size(); r-- > 0;) offs[next++] = js[r];  // descending j
+            slots[sl].first = static_cast<uint32_t>(i);
+            slots[sl].count = static_cast<uint32_t>(e - i);
+            for (size_t r = i; r < e; ++r) offs[r] = grams[r].second;  // descending j within the run
+            i = e;
         }
     }
     // Border table (Knuth-Morris-Pratt): fail[q] = length of the longest

@@ -344,6 +344,32 @@ def run_ours(args, world, rank, local):
     scanned = w.scanned_bytes
     value = world * scanned / per_step_max / 1e9
 
+    # GB/s per (text, m) cell: each cell's searches as one graph-captured
+    # batch, timed alone (L2 flushed before each), outside the step timing.
+    per_cell = {}
+    if w.name.startswith("sweep") and not args.no_cells:
+        cells = {}
+        for i, q in enumerate(queries):
+            cells.setdefault((q.text_id, len(q.pattern)), []).append(i)
+        for (ti, m), idx in sorted(cells.items()):
+            b = smg.Batch([(texts_d[ti], plans[i], outbuf[int(offs[i]):int(offs[i + 1])], counts[i:i + 1])
+                           for i in idx], graph=True)
+            ts = []
+            for r in range(3):
+                flush.zero_()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                b.launch(stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if r:
+                    ts.append(e0.elapsed_time(e1) / 1e3)
+            b.free()
+            t = min(ts)
+            name = w.specs[ti].name or f"text{ti}"
+            per_cell.setdefault(name, {})[str(m)] = round(len(idx) * len(texts_h[ti]) / t / 1e9, 1)
+
     # parity sample (outside the timed region)
     import oracle
     rng = np.random.default_rng(0)
@@ -445,6 +471,7 @@ def run_ours(args, world, rank, local):
         "clocks": clk,
         "gpu_launches": int(launches),
         "parity_sample": {"searches": len(sample), "ok": parity_ok},
+        "per_sigma_m_GBs": per_cell or None,
         "tuning": tuning,
     }
 
@@ -853,6 +880,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cells", action="store_true", help="skip the per-(sigma, m) table")
     ap.add_argument("--no-tune", action="store_true", help="keep the built-in kernel rule")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0)

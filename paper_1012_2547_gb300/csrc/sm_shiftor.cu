@@ -373,19 +373,19 @@ __device__ __forceinline__ void so_emit(const uint32_t (&F)[SO_SEGC], Put put) {
         Q[w] = (__brev(F[2 * w]) >> 16) | (2 * w + 1 < SO_SEGC ? __brev(F[2 * w + 1]) : 0u);
     uint64_t w0 = Q[0] | (static_cast<uint64_t>(Q[1]) << 32);
     uint64_t w1 = Q[2] | (static_cast<uint64_t>(Q[3]) << 32);
-    uint32_t w2 = Q[4];
+    uint64_t w2 = Q[4];
+    // Branch-free step: lanes whose next hit lies in different words run
+    // the same instructions (selects), so the warp does not serialise the
+    // three cases.
     while (w0 | w1 | w2) {
-        uint32_t b;
-        if (w0) {
-            b = __ffsll(static_cast<long long>(w0)) - 1;
-            w0 &= w0 - 1;
-        } else if (w1) {
-            b = 63 + __ffsll(static_cast<long long>(w1));
-            w1 &= w1 - 1;
-        } else {
-            b = 127 + __ffs(w2);
-            w2 &= w2 - 1;
-        }
+        const bool in0 = w0 != 0;
+        const bool in1 = !in0 && w1 != 0;
+        const uint64_t w = in0 ? w0 : (in1 ? w1 : w2);
+        const uint32_t b = (in0 ? 0u : (in1 ? 64u : 128u)) + (__ffsll(static_cast<long long>(w)) - 1);
+        const uint64_t rest = w & (w - 1);
+        w0 = in0 ? rest : w0;
+        w1 = in1 ? rest : w1;
+        w2 = (in0 || in1) ? w2 : rest;
         put(b);
     }
 }

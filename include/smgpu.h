@@ -230,8 +230,16 @@ sm_status sm_search_batch_async(const sm_query *queries, uint32_t nq, void *work
  * records the whole batch (workspace reset + one persistent launch per
  * kernel family) as a CUDA graph; sm_batch_launch replays it on `stream`.
  * The texts, plans and output buffers named by the queries must stay valid
- * for the life of the batch.  flags: 0 = capture a CUDA graph; 1 = plain
- * launches (no graph).
+ * for the life of the batch.  flags: bit 0 set = plain launches (no graph);
+ * bit 1 set = no multi-pattern packs.
+ *
+ * Multi-pattern packs (sm_search_batch, sm_search_batch_async and
+ * sm_batch_create unless flag bit 1): Shift-Or queries with m <= 16 on the
+ * same text (same pointer and length), prepared with an alphabet-size hint
+ * sigma such that sigma^m >= 2^14 (occurrences expected sparse), are packed
+ * side by side into one 32-bit Shift-And state (at most 32 bits and 16
+ * patterns a pack) and scanned together.  Results are the same as without
+ * packing for any text (dense texts are only slower).
  */
 sm_status sm_batch_create(const sm_query *queries, uint32_t nq, uint32_t flags,
                           sm_stream_t stream, sm_batch **out_batch);

@@ -278,11 +278,12 @@ class Batch:
     Keeps references to the tensors and plans it names so they outlive it.
     """
 
-    def __init__(self, items, graph: bool = True, stream=None):
+    def __init__(self, items, graph: bool = True, stream=None, pack: bool = True):
         self._keep = list(items)
         arr = _queries(self._keep)
         h = ctypes.c_void_p()
-        check(_lib.load().sm_batch_create(arr, len(self._keep), 0 if graph else 1,
+        flags = (0 if graph else 1) | (0 if pack else 2)
+        check(_lib.load().sm_batch_create(arr, len(self._keep), flags,
                                           _stream_ptr(stream), ctypes.byref(h)), "sm_batch_create")
         self._h = h.value
 

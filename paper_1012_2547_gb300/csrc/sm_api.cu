@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -32,6 +33,8 @@ uint64_t so_tile_starts();
 uint32_t so_hit_buffer();
 uint32_t so_spill_bytes();
 uint32_t so_max_sub();
+const void *mp_kernel_fn();
+size_t mp_kernel_smem();
 const void *qg_kernel_fn(int kid);
 int qg_kernel_threads();
 }  // namespace smgpu
@@ -217,6 +220,7 @@ struct sm_plan {
     std::shared_ptr<DevArena> arena;
     int kid = 0;
     uint32_t min_units = 1;  // shortest work item in units (config `tile`, bit-parallel kernels)
+    uint32_t sigma = 0;      // alphabet-size hint given at preparation (0 = unknown)
     std::vector<uint8_t> pattern;
 };
 
@@ -450,6 +454,7 @@ sm_status prepare_many(const uint8_t *patterns, const uint32_t *lengths, uint32_
         pl->arena = arena;
         pl->kid = kids[i];
         pl->min_units = min_units[i];
+        pl->sigma = sigma;
         pl->pattern.assign(patterns + pos, patterns + pos + lengths[i]);
         pos += lengths[i];
         out[i] = pl;
@@ -493,7 +498,7 @@ uint32_t sub_per_item(int kid, uint64_t units) {
     const KernelShape &s = lib().shapes[kid];
     const uint64_t resident = static_cast<uint64_t>(lib().sms) * std::max(1, s.blocks_per_sm);
     const uint64_t per = (units + 4 * resident - 1) / (4 * resident);
-    const uint64_t cap = so_kid(kid) ? std::min<uint64_t>(lib().item_cap, so_max_sub())
+    const uint64_t cap = staged_kid(kid) ? std::min<uint64_t>(lib().item_cap, so_max_sub())
                                         : lib().item_cap;
     return static_cast<uint32_t>(std::max<uint64_t>(1, std::min<uint64_t>(cap, per)));
 }
@@ -527,10 +532,10 @@ cudaError_t kernels_init(int sms) {
     (void)sms;
     for (int k = 0; k < K_COUNT; ++k) {
         KernelShape &s = g_shapes[k];
-        if (so_kid(k)) {
-            s.fn = so_kernel_fn(k);
+        if (staged_kid(k)) {
+            s.fn = k == K_SOMULTI ? mp_kernel_fn() : so_kernel_fn(k);
             s.threads = so_kernel_threads();
-            s.smem = so_kernel_smem(k);
+            s.smem = k == K_SOMULTI ? mp_kernel_smem() : so_kernel_smem(k);
             cudaError_t e = cudaFuncSetAttribute(s.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  static_cast<int>(s.smem));
             if (e != cudaSuccess) return e;
@@ -625,39 +630,103 @@ struct BatchLayout {
     size_t bytes = 0;
     size_t desc_off = 0;
     size_t zero_off = 0;
+    size_t pack_off = 0;
     std::vector<QueryDev> desc;
     std::vector<uint64_t *> zero;
+    std::vector<uint8_t> packs;  // PackPlan blocks, MP_PLAN_BYTES each
 };
 
-sm_status batch_layout(const sm_query *qs, uint32_t nq, uint8_t *base, sm_batch *b, BatchLayout *L) {
+// A pattern can join a multi-pattern pack: Shift-And with a 1- or 2-byte
+// mask table (m <= 16) and a known alphabet size with sigma^m >= 2^14, so
+// that its occurrences are expected sparse (the packed scan rescans the
+// 16-byte chunks that hold one).
+bool packable(const sm_plan *p) {
+    if (p->kid != K_SO8H && p->kid != K_SO16H) return false;
+    if (p->sigma < 2) return false;
+    return static_cast<double>(p->hdr.m) * std::log2(static_cast<double>(p->sigma)) >= 14.0;
+}
+
+// Lays a batch out at `base` (null: sizes only).  Queries are grouped by
+// kernel, keeping input order inside a group.  With `pack`, packable
+// queries on the same text (pointer and length) are first grouped into
+// multi-pattern packs (first fit by decreasing m: at most 32 bits and
+// MP_MAXK patterns a pack); a pack of one pattern stays a plain query.
+sm_status batch_layout(const sm_query *qs, uint32_t nq, uint8_t *base, sm_batch *b, BatchLayout *L,
+                       bool pack = true) {
     for (uint32_t i = 0; i < nq; ++i)
         if (!query_ok(qs[i].text, qs[i].n, qs[i].plan, qs[i].out_pos, qs[i].cap, qs[i].out_count))
             return SM_EINVAL;
     sm_status st = ensure_init();
     if (st != SM_OK) return st;
-    // Group by kernel, keeping input order inside a group.
     std::vector<std::vector<uint32_t>> by_kid(K_COUNT);
     L->zero.clear();
     L->desc.clear();
+    L->packs.clear();
     b->groups.clear();
     std::vector<uint64_t> units(nq), ntiles(nq);
-    uint64_t group_units[K_COUNT] = {};
     for (uint32_t i = 0; i < nq; ++i) {
         units[i] = kernel_ntiles(qs[i].plan->kid, qs[i].plan->hdr, qs[i].text, qs[i].n);
         if (units[i] == 0) L->zero.push_back(qs[i].out_count);
-        else {
-            by_kid[qs[i].plan->kid].push_back(i);
-            group_units[qs[i].plan->kid] += units[i];
+    }
+
+    // ---- multi-pattern packs
+    std::vector<std::vector<uint32_t>> packs;
+    std::vector<char> in_pack(nq, 0);
+    if (pack) {
+        std::map<std::pair<uintptr_t, uint64_t>, std::vector<uint32_t>> by_text;
+        for (uint32_t i = 0; i < nq; ++i)
+            if (units[i] && packable(qs[i].plan))
+                by_text[{reinterpret_cast<uintptr_t>(qs[i].text), qs[i].n}].push_back(i);
+        for (auto &kv : by_text) {
+            std::vector<uint32_t> &v = kv.second;
+            if (v.size() < 2) continue;
+            std::stable_sort(v.begin(), v.end(), [&](uint32_t x, uint32_t y) {
+                return qs[x].plan->hdr.m > qs[y].plan->hdr.m;
+            });
+            std::vector<std::vector<uint32_t>> local;
+            std::vector<uint32_t> bits;
+            for (uint32_t i : v) {
+                const uint32_t m = qs[i].plan->hdr.m;
+                size_t j = 0;
+                while (j < local.size() && (bits[j] + m > 32 || local[j].size() >= MP_MAXK)) ++j;
+                if (j == local.size()) {
+                    local.emplace_back();
+                    bits.push_back(0);
+                }
+                local[j].push_back(i);
+                bits[j] += m;
+            }
+            for (auto &pk : local) {
+                if (pk.size() < 2) continue;
+                for (uint32_t i : pk) in_pack[i] = 1;
+                packs.push_back(std::move(pk));
+            }
         }
     }
+
+    uint64_t group_units[K_COUNT] = {};
+    for (uint32_t i = 0; i < nq; ++i) {
+        if (units[i] == 0 || in_pack[i]) continue;
+        by_kid[qs[i].plan->kid].push_back(i);
+        group_units[qs[i].plan->kid] += units[i];
+    }
+    for (const auto &pk : packs) group_units[K_SOMULTI] += units[pk[0]];
     uint32_t group_per[K_COUNT];
     for (int k = 0; k < K_COUNT; ++k) group_per[k] = sub_per_item(k, group_units[k]);
     std::vector<uint32_t> per_q(nq, 1);
     for (uint32_t i = 0; i < nq; ++i) {
-        if (units[i] == 0) continue;
+        if (units[i] == 0 || in_pack[i]) continue;
         per_q[i] = balanced_per(units[i], std::max(group_per[qs[i].plan->kid], qs[i].plan->min_units));
         ntiles[i] = (units[i] + per_q[i] - 1) / per_q[i];
     }
+    std::vector<uint32_t> per_pack(packs.size());
+    std::vector<uint64_t> ntiles_pack(packs.size());
+    for (size_t j = 0; j < packs.size(); ++j) {
+        const uint64_t u = units[packs[j][0]];
+        per_pack[j] = balanced_per(u, group_per[K_SOMULTI]);
+        ntiles_pack[j] = (u + per_pack[j] - 1) / per_pack[j];
+    }
+
     uint64_t total_states = 0;
     size_t ndesc = 0;
     for (int k = 0; k < K_COUNT; ++k)
@@ -665,21 +734,47 @@ sm_status batch_layout(const sm_query *qs, uint32_t nq, uint8_t *base, sm_batch 
             total_states += ntiles[i];
             ++ndesc;
         }
+    size_t nmembers = 0;
+    for (size_t j = 0; j < packs.size(); ++j) {
+        total_states += packs[j].size() * ntiles_pack[j];
+        nmembers += packs[j].size();
+    }
+    ndesc += packs.size() + nmembers;  // pack heads, then the packed patterns' own queries
     const size_t states_off = kTicketBytes;
     L->desc_off = align16(states_off + total_states * sizeof(uint64_t));
     L->zero_off = align16(L->desc_off + ndesc * sizeof(QueryDev));
-    size_t spill_need = 0;  // bit-parallel groups run one after another: share one area
-    for (int k = 0; so_kid(k); ++k) {
-        if (by_kid[k].empty()) continue;
+    L->pack_off = (L->zero_off + L->zero.size() * sizeof(uint64_t *) + 255) & ~size_t(255);
+    size_t spill_need = 0;  // staged groups run one after another: they share one area
+    for (int k = 0; k < K_COUNT; ++k) {
+        if (!staged_kid(k)) continue;
         uint64_t t = 0;
-        for (uint32_t i : by_kid[k]) t += ntiles[i];
-        spill_need = std::max(spill_need, static_cast<size_t>(grid_for(k, t)) * so_spill_bytes());
+        if (k == K_SOMULTI)
+            for (uint64_t x : ntiles_pack) t += x;
+        else
+            for (uint32_t i : by_kid[k]) t += ntiles[i];
+        if (t) spill_need = std::max(spill_need, static_cast<size_t>(grid_for(k, t)) * so_spill_bytes());
     }
-    const size_t spill_off = (L->zero_off + L->zero.size() * sizeof(uint64_t *) + 255) & ~size_t(255);
+    const size_t spill_off = (L->pack_off + packs.size() * MP_PLAN_BYTES + 255) & ~size_t(255);
     L->bytes = spill_off + spill_need + 16;
     L->desc.reserve(ndesc);
     uint64_t state_pos = 0;
     int gi = 0;
+    auto add_group = [&](int k, size_t first_desc, uint32_t count, uint64_t tickets) -> sm_status {
+        if (gi >= static_cast<int>(kTicketBytes / 8)) return SM_EINVAL;
+        sm_batch::Group g{};
+        g.kid = k;
+        g.args.qs = reinterpret_cast<const QueryDev *>(base + L->desc_off) + first_desc;
+        g.args.nq = count;
+        if (count == 1) g.args.one = L->desc[first_desc];
+        g.args.ticket = reinterpret_cast<unsigned long long *>(base) + gi;
+        g.args.total = tickets;
+        g.args.err = lib().err;
+        g.args.spill = staged_kid(k) ? base + spill_off : nullptr;
+        g.grid = grid_for(k, tickets);
+        b->groups.push_back(g);
+        ++gi;
+        return SM_OK;
+    };
     for (int k = 0; k < K_COUNT; ++k) {
         if (by_kid[k].empty()) continue;
         const size_t first_desc = L->desc.size();
@@ -701,19 +796,64 @@ sm_status batch_layout(const sm_query *qs, uint32_t nq, uint8_t *base, sm_batch 
             state_pos += ntiles[i];
             L->desc.push_back(d);
         }
-        if (gi >= static_cast<int>(kTicketBytes / 8)) return SM_EINVAL;
-        sm_batch::Group g{};
-        g.kid = k;
-        g.args.qs = reinterpret_cast<const QueryDev *>(base + L->desc_off) + first_desc;
-        g.args.nq = static_cast<uint32_t>(by_kid[k].size());
-        if (g.args.nq == 1) g.args.one = L->desc[first_desc];
-        g.args.ticket = reinterpret_cast<unsigned long long *>(base) + gi;
-        g.args.total = ticket;
-        g.args.err = lib().err;
-        g.args.spill = so_kid(k) ? base + spill_off : nullptr;
-        g.grid = grid_for(k, ticket);
-        b->groups.push_back(g);
-        ++gi;
+        st = add_group(k, first_desc, static_cast<uint32_t>(by_kid[k].size()), ticket);
+        if (st != SM_OK) return st;
+    }
+    if (!packs.empty()) {
+        // Heads first (the kernel's queries), then the members.
+        const size_t first_head = L->desc.size();
+        const size_t first_member = first_head + packs.size();
+        L->packs.assign(packs.size() * MP_PLAN_BYTES, 0);
+        uint64_t ticket = 0;
+        size_t mi = first_member;
+        std::vector<QueryDev> members;
+        members.reserve(nmembers);
+        for (size_t j = 0; j < packs.size(); ++j) {
+            const uint32_t h = packs[j][0];
+            QueryDev d{};
+            d.text = qs[h].text;
+            d.n = qs[h].n;
+            d.plan = reinterpret_cast<const PlanDev *>(base + L->pack_off + j * MP_PLAN_BYTES);
+            d.ntiles = ntiles_pack[j];
+            d.first_ticket = ticket;
+            d.nsub = units[h];
+            d.sub_per_item = per_pack[j];
+            ticket += ntiles_pack[j];
+            L->desc.push_back(d);
+            PackPlan &P = *reinterpret_cast<PackPlan *>(L->packs.data() + j * MP_PLAN_BYTES);
+            P.k = static_cast<uint32_t>(packs[j].size());
+            uint32_t shift = 0;
+            for (uint32_t t = 0; t < P.k; ++t) {
+                const uint32_t i = packs[j][t];
+                const sm_plan *pl = qs[i].plan;
+                const uint32_t m = pl->hdr.m;
+                P.shift[t] = static_cast<uint8_t>(shift);
+                P.len[t] = static_cast<uint8_t>(m);
+                P.I |= 1u << shift;
+                P.F |= 1u << (shift + m - 1);
+                P.maxm = std::max(P.maxm, m);
+                for (uint32_t q = 0; q < m; ++q) P.table[pl->pattern[q]] |= 1u << (shift + q);
+                P.member[t] = reinterpret_cast<const QueryDev *>(base + L->desc_off) + mi;
+                QueryDev md{};
+                md.text = qs[i].text;
+                md.n = qs[i].n;
+                md.plan = pl->dev;
+                md.out_pos = qs[i].out_pos;
+                md.cap = qs[i].cap;
+                md.out_count = qs[i].out_count;
+                md.state = reinterpret_cast<uint64_t *>(base + states_off) + state_pos;
+                md.ntiles = ntiles_pack[j];
+                md.nsub = units[h];
+                md.sub_per_item = per_pack[j];
+                state_pos += ntiles_pack[j];
+                members.push_back(md);
+                ++mi;
+                shift += m;
+            }
+        }
+        L->desc.insert(L->desc.end(), members.begin(), members.end());
+        st = add_group(K_SOMULTI, first_head, static_cast<uint32_t>(packs.size()), ticket);
+        if (st != SM_OK) return st;
     }
     b->base = base;
     b->zero_list = reinterpret_cast<uint64_t **>(base + L->zero_off);
@@ -723,23 +863,35 @@ sm_status batch_layout(const sm_query *qs, uint32_t nq, uint8_t *base, sm_batch 
     return SM_OK;
 }
 
-// Builds a batch in its own device allocation (descriptors copied with a
-// blocking copy).
-sm_status batch_build(const sm_query *qs, uint32_t nq, sm_batch *b) {
+// Copies a laid-out batch's descriptors, zero list and packs to `base`
+// (pageable sources: each copy returns once its bytes are staged).
+sm_status batch_upload(const BatchLayout &L, uint8_t *base, cudaStream_t stream) {
+    if (!L.desc.empty())
+        SM_TRY_CUDA(cudaMemcpyAsync(base + L.desc_off, L.desc.data(), L.desc.size() * sizeof(QueryDev),
+                                    cudaMemcpyHostToDevice, stream));
+    if (!L.zero.empty())
+        SM_TRY_CUDA(cudaMemcpyAsync(base + L.zero_off, L.zero.data(), L.zero.size() * sizeof(uint64_t *),
+                                    cudaMemcpyHostToDevice, stream));
+    if (!L.packs.empty())
+        SM_TRY_CUDA(cudaMemcpyAsync(base + L.pack_off, L.packs.data(), L.packs.size(),
+                                    cudaMemcpyHostToDevice, stream));
+    return SM_OK;
+}
+
+// Builds a batch in its own device allocation (descriptors copied with
+// blocking copies).
+sm_status batch_build(const sm_query *qs, uint32_t nq, sm_batch *b, bool pack = true) {
     BatchLayout L;
-    sm_status st = batch_layout(qs, nq, nullptr, b, &L);
+    sm_status st = batch_layout(qs, nq, nullptr, b, &L, pack);
     if (st != SM_OK) return st;
     auto arena = std::make_shared<DevArena>();
     SM_TRY_CUDA(cudaMalloc(&arena->ptr, L.bytes));
     uint8_t *base = static_cast<uint8_t *>(arena->ptr);
-    st = batch_layout(qs, nq, base, b, &L);
+    st = batch_layout(qs, nq, base, b, &L, pack);
     if (st != SM_OK) return st;
-    if (!L.desc.empty())
-        SM_TRY_CUDA(cudaMemcpy(base + L.desc_off, L.desc.data(), L.desc.size() * sizeof(QueryDev),
-                               cudaMemcpyHostToDevice));
-    if (!L.zero.empty())
-        SM_TRY_CUDA(cudaMemcpy(base + L.zero_off, L.zero.data(), L.zero.size() * sizeof(uint64_t *),
-                               cudaMemcpyHostToDevice));
+    st = batch_upload(L, base, nullptr);
+    if (st != SM_OK) return st;
+    SM_TRY_CUDA(cudaStreamSynchronize(nullptr));
     b->arena = arena;
     return SM_OK;
 }
@@ -870,13 +1022,8 @@ sm_status sm_search_batch_async(const sm_query *queries, uint32_t nq, void *work
     uint8_t *base = static_cast<uint8_t *>(workspace);
     st = batch_layout(queries, nq, base, &b, &L);
     if (st != SM_OK) return st;
-    // Pageable sources: each copy returns once its bytes are staged.
-    if (!L.desc.empty())
-        SM_TRY_CUDA(cudaMemcpyAsync(base + L.desc_off, L.desc.data(), L.desc.size() * sizeof(QueryDev),
-                                    cudaMemcpyHostToDevice, stream));
-    if (!L.zero.empty())
-        SM_TRY_CUDA(cudaMemcpyAsync(base + L.zero_off, L.zero.data(),
-                                    L.zero.size() * sizeof(uint64_t *), cudaMemcpyHostToDevice, stream));
+    st = batch_upload(L, base, stream);
+    if (st != SM_OK) return st;
     return batch_enqueue(&b, stream);
 }
 
@@ -885,7 +1032,7 @@ sm_status sm_batch_create(const sm_query *queries, uint32_t nq, uint32_t flags, 
     (void)stream;
     if (!out_batch || (nq > 0 && !queries)) return SM_EINVAL;
     sm_batch *b = new sm_batch();
-    sm_status st = nq ? batch_build(queries, nq, b) : SM_OK;
+    sm_status st = nq ? batch_build(queries, nq, b, !(flags & 2u)) : SM_OK;
     if (st != SM_OK) {
         delete b;
         return st;

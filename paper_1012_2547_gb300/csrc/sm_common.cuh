@@ -71,6 +71,24 @@ struct LaunchArgs {
 
 enum : uint32_t { ERR_TIMEOUT = 1u, ERR_COPY = 2u };
 
+// A multi-pattern pack, built by the host for a batch: up to MP_MAXK
+// Shift-And patterns over one text, packed side by side into one 32-bit
+// state.  The pack's own QueryDev (text, item split, tickets) has `plan`
+// pointing at this block; each pattern keeps its own query (output,
+// capacity, count, look-back words).
+constexpr int MP_MAXK = 16;
+struct PackPlan {
+    uint32_t k;                       // patterns in the pack
+    uint32_t I;                       // the first bit of every field
+    uint32_t F;                       // the last bit of every field
+    uint32_t maxm;                    // longest pattern
+    uint8_t shift[MP_MAXK];           // field of pattern p: bits shift[p] ..
+    uint8_t len[MP_MAXK];             //   shift[p] + len[p] - 1 (len = m)
+    const QueryDev *member[MP_MAXK];  // the patterns' own queries
+    uint32_t table[256];              // OR over p of (mask_p[c] << shift[p])
+};
+constexpr size_t MP_PLAN_BYTES = (sizeof(PackPlan) + 255) & ~size_t(255);
+
 // Look-back word: status in bits 62..63, value in bits 0..61.
 constexpr uint64_t LB_EMPTY = 0ull;
 constexpr uint64_t LB_AGG = 1ull << 62;

@@ -22,10 +22,13 @@ enum KernelId : int {
     K_SO64A = 5,  // 64-bit state, m <= 64
     K_QGRAM = 6,  // exact q-gram stride filter + warp verification
     K_LINEAR = 7, // per-segment Knuth-Morris-Pratt
-    K_COUNT = 8
+    K_SOMULTI = 8, // several Shift-And patterns (m <= 16) of one text in one state (batches only)
+    K_COUNT = 9
 };
 
 inline bool so_kid(int kid) { return kid <= K_SO64A; }
+// Kernels that stage sub-tiles and use the per-block spill area.
+inline bool staged_kid(int kid) { return kid <= K_SO64A || kid == K_SOMULTI; }
 inline uint32_t so_entry_bytes(int kid) {
     return kid == K_SO8H ? 1u : kid == K_SO16H ? 2u : (kid <= K_SO32A ? 4u : 8u);
 }

@@ -668,6 +668,417 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
     if (have_pending) write_pending();
 }
 
+// ---------------------------------------------------------------- multi-pattern packs
+//
+// Up to MP_MAXK patterns of at most 16 bytes over one text share one 32-bit
+// state: pattern p owns bits shift[p] .. shift[p] + m_p - 1.  One step for
+// all of them (the Shift-And recurrence of each field side by side):
+//     D <- ((D << 1) | I) & B[c],   I = the first bit of every field,
+// where B[c] is the OR of the patterns' masks, each shifted to its field (a
+// bit carried out of a field's top lands on the next field's first bit,
+// which the OR with I sets anyway).  Pattern p has an occurrence ending at
+// e iff bit shift[p] + m_p - 1 (a bit of F) of D is set.  The scan ORs the
+// states of each 16-byte chunk; a chunk whose OR meets F is rescanned byte
+// by byte to name the (pattern, position) pairs.  The segment's start
+// state comes from a warm-up over the 16 bytes before it (every field is at
+// most 16 bits, so all fields are exact after it).
+
+constexpr int MP_REC = 4;  // (pattern, position) records a lane keeps per sub-tile
+
+struct MPLayout {
+    static constexpr uint32_t BAR_OFF = SO_NBUF * SO_BUF;
+    static constexpr uint32_t CONST_OFF = BAR_OFF + 8 * SO_NBUF;
+    static constexpr uint32_t CNT_OFF = CONST_OFF + 16;         // hits per pattern, current item
+    static constexpr uint32_t PCNT_OFF = CNT_OFF + 4 * MP_MAXK;  // hits per pattern, pending item
+    static constexpr uint32_t FMAP_OFF = PCNT_OFF + 4 * MP_MAXK; // last bit -> pattern
+    static constexpr uint32_t BYTES = FMAP_OFF + 32;
+};
+
+struct MPItem {
+    uint32_t qi;
+    uint64_t k, sb, se;
+    uint32_t listed;  // records in the spill list
+    bool overflow;    // records were lost: the write phase rescans per pattern
+};
+
+// Loads a pack's table and constants into shared memory unless loaded.
+__device__ __forceinline__ void mp_table(const PackPlan *P, const PackPlan *&cur, uint32_t *tbl,
+                                         uint8_t *fmap) {
+    if (P == cur) return;
+    __syncwarp();
+    const int lane = threadIdx.x & 31;
+    const uint4 *src = reinterpret_cast<const uint4 *>(P->table);
+    for (int c = lane; c < 64; c += 32) reinterpret_cast<uint4 *>(tbl)[c] = __ldg(&src[c]);
+    const uint32_t k = __ldg(&P->k);
+    fmap[lane] = 0xFF;
+    __syncwarp();
+    if (lane < static_cast<int>(k)) fmap[__ldg(&P->shift[lane]) + __ldg(&P->len[lane]) - 1] = static_cast<uint8_t>(lane);
+    cur = P;
+    __syncwarp();
+}
+
+// Entry of byte b of word x from the packed table at shared address tb
+// (4-byte entries: address c * four + tb on the FMA pipe).
+__device__ __forceinline__ uint32_t mp_entry(uint32_t x, int b, uint32_t tb, uint32_t four) {
+    const uint32_t addr = __byte_perm(x, 0u, 0x4440u | b) * four + tb;
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+
+// Four packed steps on the bytes of x; A collects the states.
+__device__ __forceinline__ void mp_step4(uint32_t &D, uint32_t &A, uint32_t x, uint32_t tb, uint32_t two,
+                                         uint32_t four, uint32_t I) {
+    uint32_t d[4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        D = ((D * two) | I) & mp_entry(x, b, tb, four);
+        d[b] = D;
+    }
+    A |= d[0] | d[1] | d[2] | d[3];
+}
+
+// Byte-by-byte rescan of a flagged chunk from its start state: every valid
+// (pattern, end) pair is counted (shared counters) and, while the lane has
+// room, kept as a record (chunk << 12 | byte << 8 | pattern).
+__device__ __noinline__ void mp_chunk(uint32_t D, uint4 w, int c, uint32_t tb, uint32_t two, uint32_t four,
+                                      uint32_t I, uint32_t F, const uint8_t *fmap, const PackPlan *P,
+                                      int64_t x, int64_t vlo0, int64_t vhi, uint32_t *cnt,
+                                      uint64_t &rec, int &nrec, bool &lost) {
+    for (int b = 0; b < 16; ++b) {
+        const uint32_t xw = b < 4 ? w.x : b < 8 ? w.y : b < 12 ? w.z : w.w;
+        D = ((D * two) | I) & mp_entry(xw, b & 3, tb, four);
+        uint32_t h = D & F;
+        const int64_t e = x + 16 * c + b;  // end position (virtual frame)
+        while (h) {
+            const int bit = __ffs(h) - 1;
+            h &= h - 1;
+            const int p = fmap[bit];
+            if (e < vlo0 + __ldg(&P->len[p]) - 1 || e >= vhi) continue;  // not a valid end of p
+            atomicAdd(&cnt[p], 1u);
+            if (nrec < MP_REC) {
+                rec |= static_cast<uint64_t>((c << 12) | (b << 8) | p) << (16 * nrec);
+                ++nrec;
+            } else {
+                lost = true;
+            }
+        }
+    }
+}
+
+// Exclusive prefix of item k of one pattern's query, walking its look-back
+// words one at a time (single lane); publishes the inclusive prefix.  The
+// walk is short: it runs one item behind the scan.
+__device__ __forceinline__ uint64_t mp_lookback(uint64_t *state, uint64_t k, uint64_t agg, uint32_t *err,
+                                                bool *ok) {
+    *ok = true;
+    if (k == 0) return 0;
+    uint64_t excl = 0;
+    int64_t j = static_cast<int64_t>(k) - 1;
+    uint32_t sleep_ns = 32;
+    uint64_t t0 = 0;
+    bool timed = false;
+    while (j >= 0) {
+        const uint64_t w = ld_relaxed(&state[j]);
+        const uint64_t st = w & ~LB_VAL;
+        if (st == LB_INC) {
+            excl += w & LB_VAL;
+            break;
+        }
+        if (st == LB_AGG) {
+            excl += w & LB_VAL;
+            --j;
+            timed = false;
+            continue;
+        }
+        if (st == LB_ERR) {
+            *ok = false;
+            break;
+        }
+        if (!timed) {
+            t0 = global_ns();
+            timed = true;
+        } else if (global_ns() - t0 > WAIT_LIMIT_NS) {
+            atomicOr(err, ERR_TIMEOUT);
+            *ok = false;
+            break;
+        }
+        __nanosleep(sleep_ns);
+        sleep_ns = min(sleep_ns * 2, 1024u);
+    }
+    st_relaxed(&state[k], *ok ? (LB_INC | ((excl + agg) & LB_VAL)) : LB_ERR);
+    return excl;
+}
+
+// One warp per block, the same work-item scheme, staging ring and one-item
+// lag as so_kernel, over packs instead of single patterns.  A work item's
+// records go to the block's spill list in position order; at its write
+// phase every pattern's prefix is resolved (lane p for pattern p) and the
+// records are scattered to the patterns' outputs with their ranks.  If a
+// lane ever had more than MP_REC records in a sub-tile, or the list filled,
+// the write phase instead rescans the item from global memory once per
+// pattern (exact for any input, slow only for dense ones).
+__global__ void __launch_bounds__(32) mp_kernel(const __grid_constant__ LaunchArgs a) {
+    using L = MPLayout;
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ __align__(256) uint32_t tbl[256];
+    const uint32_t tb = smem_addr(tbl);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L::BAR_OFF);
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(smem + L::CNT_OFF);
+    uint32_t *pcnt = reinterpret_cast<uint32_t *>(smem + L::PCNT_OFF);
+    uint8_t *fmap = smem + L::FMAP_OFF;
+    const int lane = threadIdx.x;
+    uint8_t *spill_base =
+        a.spill ? a.spill + static_cast<size_t>(blockIdx.x) * SO_SPILL_BYTES : nullptr;
+    volatile uint32_t *consts = reinterpret_cast<volatile uint32_t *>(smem + L::CONST_OFF);
+
+    unsigned long long t = 0;
+    uint32_t qi = 0;
+    uint64_t k = 0;
+    if (lane == 0) {
+        consts[0] = 2u;
+        consts[1] = 4u;
+        for (int b = 0; b < SO_NBUF; ++b) mbar_init(&bar[b], 1);
+        fence_mbar_init();
+        if (so_claim(a, &t, &qi, &k)) {
+            const QueryDev &Q = query_of(a, qi);
+            const uint64_t s0 = k * Q.sub_per_item;
+            const uint64_t s1 = min(s0 + Q.sub_per_item, Q.nsub);
+            for (int i = 0; i < SO_NBUF - 1 && s0 + i < s1; ++i)
+                so_issue(smem + i * SO_BUF, &bar[i], Q.text, Q.n, s0 + i);
+        } else {
+            t = a.total;
+        }
+    }
+    __syncwarp();
+    t = __shfl_sync(0xffffffffu, t, 0);
+    qi = __shfl_sync(0xffffffffu, qi, 0);
+    k = __shfl_sync(0xffffffffu, k, 0);
+    const uint32_t two = consts[0];
+    const uint32_t four = consts[1];
+
+    const PackPlan *cur_pack = nullptr;
+    uint32_t parity = 0;
+    int cur = 0;
+    int hb = 0;
+    bool have_pending = false;
+    MPItem pend{};
+
+    auto write_pending = [&]() {
+        const QueryDev &Q = query_of(a, pend.qi);
+        const PackPlan *P = reinterpret_cast<const PackPlan *>(Q.plan);
+        const uint32_t kk = __ldg(&P->k);
+        const int64_t o = static_cast<int64_t>(reinterpret_cast<uintptr_t>(Q.text) & 15u);
+        const int64_t ivstart = static_cast<int64_t>(pend.sb) * SO_T;
+        // Lane p: pattern p's prefix, count and output.
+        uint64_t excl = 0, capp = 0;
+        uint64_t *outp = nullptr;
+        int64_t shiftp = 0;
+        bool ok = true;
+        if (lane < static_cast<int>(kk)) {
+            const QueryDev &M = *P->member[lane];
+            const uint64_t agg = pcnt[lane];
+            excl = mp_lookback(M.state, pend.k, agg, a.err, &ok);
+            if (ok && pend.k + 1 == M.ntiles) *M.out_count = excl + agg;
+            capp = M.cap;
+            outp = M.out_pos;
+            shiftp = static_cast<int64_t>(__ldg(&P->len[lane])) - 1 + o;
+        }
+        if (!__all_sync(0xffffffffu, ok)) return;
+        if (!pend.overflow) {
+            const uint32_t *list = reinterpret_cast<const uint32_t *>(spill_base + (hb ^ 1) * SO_SPILL_ITEM);
+            uint32_t basep = 0;  // lane p: records of pattern p written so far
+            for (uint32_t c0 = 0; c0 < pend.listed; c0 += 32) {
+                const bool valid = c0 + lane < pend.listed;
+                const uint32_t e = valid ? list[c0 + lane] : 0u;
+                const int p = valid ? static_cast<int>(e >> 19) : 31;
+                const uint32_t rel = e & 0x7FFFFu;
+                const unsigned peers = __match_any_sync(0xffffffffu, p);
+                const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+                const uint64_t ex = __shfl_sync(0xffffffffu, excl, p);
+                const uint64_t cp = __shfl_sync(0xffffffffu, capp, p);
+                uint64_t *op = reinterpret_cast<uint64_t *>(
+                    __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(outp), p));
+                const int64_t sh = __shfl_sync(0xffffffffu, shiftp, p);
+                const uint32_t bp = __shfl_sync(0xffffffffu, basep, p);
+                const uint64_t idx = ex + bp + rank;
+                if (valid && idx < cp) op[idx] = static_cast<uint64_t>(ivstart + rel - sh);
+                for (uint32_t q = 0; q < kk; ++q) {
+                    const unsigned mq = __ballot_sync(0xffffffffu, valid && p == static_cast<int>(q));
+                    if (lane == static_cast<int>(q)) basep += __popc(mq);
+                }
+            }
+            return;
+        }
+        // Overflow: one pass per pattern over the item's text in global
+        // memory, with that pattern's own masks (its field of the table).
+        mp_table(P, cur_pack, tbl, fmap);
+        const uint8_t *base = Q.text - o;
+        const int64_t vhi = o + static_cast<int64_t>(Q.n);
+        const int64_t vlim = (vhi + 15) & ~int64_t(15);
+        for (uint32_t p = 0; p < kk; ++p) {
+            const uint64_t ex = __shfl_sync(0xffffffffu, excl, p);
+            const uint64_t cp = __shfl_sync(0xffffffffu, capp, p);
+            uint64_t *op = reinterpret_cast<uint64_t *>(
+                __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(outp), p));
+            const int64_t sh = __shfl_sync(0xffffffffu, shiftp, p);
+            const uint32_t sp = __ldg(&P->shift[p]);
+            const uint32_t mpl = __ldg(&P->len[p]);
+            const uint32_t low = (mpl >= 32 ? 0xFFFFFFFFu : ((1u << mpl) - 1u));
+            const int64_t vlo = o + static_cast<int64_t>(mpl) - 1;
+            uint64_t run = ex;
+            for (uint64_t s = pend.sb; s < pend.se && run < cp; ++s) {
+                const int64_t x = static_cast<int64_t>(s) * SO_T + lane * SO_S;
+                uint32_t F[SO_SEGC];
+                uint32_t D = 0;
+                for (int64_t y = x - 16; y < x + SO_S; ++y) {
+                    const uint32_t cbyte = (y >= 0 && y < vlim) ? base[y] : 0u;
+                    D = ((D << 1) | 1u) & ((tbl[cbyte] >> sp) & low);
+                    if (y >= x) {
+                        const int r = static_cast<int>(y - x);
+                        if ((r & 15) == 0) F[r >> 4] = 0;
+                        F[r >> 4] |= ((D >> (mpl - 1)) & 1u) << (15 - (r & 15));
+                    }
+                }
+                const int elo = static_cast<int>(vlo - x > 0 ? vlo - x : int64_t(0));
+                const int ehi = static_cast<int>(vhi - x < SO_S ? vhi - x : int64_t(SO_S));
+                const uint32_t c = so_mask_count(F, elo, ehi);
+                uint32_t total;
+                const uint32_t exl = warp_excl_scan(c, &total);
+                so_write_flags(F, exl, run, cp, op, static_cast<int64_t>(s) * SO_T - sh);
+                run += total;
+            }
+        }
+    };
+
+    while (t < a.total) {
+        const QueryDev &Q = query_of(a, qi);
+        const PackPlan *P = reinterpret_cast<const PackPlan *>(Q.plan);
+        mp_table(P, cur_pack, tbl, fmap);
+        const uint32_t I = __ldg(&P->I);
+        const uint32_t F = __ldg(&P->F);
+        const uint8_t *const qtext = Q.text;
+        const uint64_t qn = Q.n;
+        const uint64_t qnsub = Q.nsub;
+        const uint64_t sb = k * Q.sub_per_item;
+        const uint64_t se = min(sb + Q.sub_per_item, qnsub);
+        const int64_t o = static_cast<int64_t>(reinterpret_cast<uintptr_t>(qtext) & 15u);
+        const int64_t vhi = o + static_cast<int64_t>(qn);
+        const int64_t ivstart = static_cast<int64_t>(sb) * SO_T;
+        uint32_t *list = spill_base ? reinterpret_cast<uint32_t *>(spill_base + hb * SO_SPILL_ITEM) : nullptr;
+        if (lane < MP_MAXK) cnt[lane] = 0;
+        __syncwarp();
+
+        uint32_t listed = 0;
+        bool overflow = list == nullptr;
+        bool failed = false;
+        int pending = 0;
+        for (uint64_t s = sb; s < se; ++s) {
+            const int ahead = cur == 0 ? SO_NBUF - 1 : cur - 1;
+            if (lane == 0 && s + SO_NBUF - 1 < se)
+                so_issue(smem + ahead * SO_BUF, &bar[ahead], qtext, qn, s + SO_NBUF - 1);
+            const bool arrived = mbar_wait_bounded(&bar[cur], (parity >> cur) & 1u);
+            parity ^= 1u << cur;
+            if (!__all_sync(0xffffffffu, arrived)) {
+                failed = true;
+                pending = 0;
+                for (int i = 1; i < SO_NBUF; ++i) pending += s + i < se;
+                break;
+            }
+            const uint8_t *seg = smem + cur * SO_BUF + SO_LHALO + lane * SO_S;
+            const int64_t x = static_cast<int64_t>(s) * SO_T + lane * SO_S;
+            uint32_t D = 0, A = 0;
+            {
+                const uint4 w = *reinterpret_cast<const uint4 *>(seg - 16);
+                mp_step4(D, A, w.x, tb, two, four, I);
+                mp_step4(D, A, w.y, tb, two, four, I);
+                mp_step4(D, A, w.z, tb, two, four, I);
+                mp_step4(D, A, w.w, tb, two, four, I);
+            }
+            uint64_t rec = 0;
+            int nrec = 0;
+            bool lost = false;
+#pragma unroll
+            for (int c = 0; c < SO_SEGC; ++c) {
+                const uint4 w = *reinterpret_cast<const uint4 *>(seg + 16 * c);
+                const uint32_t Ds = D;
+                A = 0;
+                mp_step4(D, A, w.x, tb, two, four, I);
+                mp_step4(D, A, w.y, tb, two, four, I);
+                mp_step4(D, A, w.z, tb, two, four, I);
+                mp_step4(D, A, w.w, tb, two, four, I);
+                if (A & F)
+                    mp_chunk(Ds, w, c, tb, two, four, I, F, fmap, P, x, o, vhi, cnt, rec, nrec, lost);
+            }
+            if (__any_sync(0xffffffffu, nrec != 0 || lost)) {
+                uint32_t total;
+                const uint32_t ex = warp_excl_scan(static_cast<uint32_t>(nrec), &total);
+                overflow |= __any_sync(0xffffffffu, lost) || listed + total > SO_SPILL_POS;
+                if (!overflow) {
+                    const uint32_t rel0 = static_cast<uint32_t>(x - ivstart);
+                    for (int r = 0; r < nrec; ++r) {
+                        const uint32_t v = static_cast<uint32_t>(rec >> (16 * r)) & 0xFFFFu;
+                        const uint32_t pos = rel0 + 16 * ((v >> 12) & 15u) + ((v >> 8) & 15u);
+                        list[listed + ex + r] = ((v & 0xFFu) << 19) | pos;
+                    }
+                }
+                listed += total;
+            }
+            __syncwarp();
+            cur = cur == SO_NBUF - 1 ? 0 : cur + 1;
+        }
+        if (failed) {
+            if (lane == 0) {
+                atomicOr(a.err, ERR_COPY);
+                for (int i = 1; i <= pending; ++i) {
+                    const int b = (cur + i) % SO_NBUF;
+                    mbar_wait_bounded(&bar[b], (parity >> b) & 1u);
+                }
+            }
+            const uint32_t kk = __ldg(&P->k);
+            if (lane < static_cast<int>(kk)) st_relaxed(&P->member[lane]->state[k], LB_ERR);
+            if (have_pending) {
+                const PackPlan *Pp = reinterpret_cast<const PackPlan *>(query_of(a, pend.qi).plan);
+                if (lane < static_cast<int>(__ldg(&Pp->k))) st_relaxed(&Pp->member[lane]->state[pend.k], LB_ERR);
+            }
+            return;
+        }
+
+        // ---- publish every pattern's count; claim and start the next item;
+        // finish the previous one.
+        __syncwarp();
+        const uint32_t kk = __ldg(&P->k);
+        if (lane < static_cast<int>(kk))
+            st_relaxed(&P->member[lane]->state[k], (k == 0 ? LB_INC : LB_AGG) | cnt[lane]);
+        unsigned long long nt = a.total;
+        uint32_t nqi = 0;
+        uint64_t nk = 0;
+        if (lane == 0 && so_claim(a, &nt, &nqi, &nk)) {
+            const QueryDev &Qn = query_of(a, nqi);
+            const uint64_t s0 = nk * Qn.sub_per_item;
+            const uint64_t s1 = min(s0 + Qn.sub_per_item, Qn.nsub);
+            for (int i = 0; i < SO_NBUF - 1 && s0 + i < s1; ++i) {
+                const int c = (cur + i) % SO_NBUF;
+                so_issue(smem + c * SO_BUF, &bar[c], Qn.text, Qn.n, s0 + i);
+            }
+        }
+        nt = __shfl_sync(0xffffffffu, nt, 0);
+        nqi = __shfl_sync(0xffffffffu, nqi, 0);
+        nk = __shfl_sync(0xffffffffu, nk, 0);
+        if (have_pending) write_pending();
+        __syncwarp();
+        if (lane < MP_MAXK) pcnt[lane] = cnt[lane];
+        pend = MPItem{qi, k, sb, se, listed, overflow};
+        have_pending = true;
+        hb ^= 1;
+        __syncwarp();
+        t = nt;
+        qi = nqi;
+        k = nk;
+    }
+    if (have_pending) write_pending();
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- registry
@@ -702,6 +1113,10 @@ uint32_t so_hit_buffer() { return SO_HITS; }
 uint32_t so_spill_bytes() { return SO_SPILL_BYTES; }
 
 uint32_t so_max_sub() { return SO_MAX_SUB; }
+
+const void *mp_kernel_fn() { return reinterpret_cast<const void *>(&mp_kernel); }
+
+size_t mp_kernel_smem() { return MPLayout::BYTES; }
 
 }  // namespace smgpu
 

@@ -722,8 +722,12 @@ sm_status batch_layout(const sm_query *qs, uint32_t nq, uint8_t *base, sm_batch 
     std::vector<uint32_t> per_pack(packs.size());
     std::vector<uint64_t> ntiles_pack(packs.size());
     for (size_t j = 0; j < packs.size(); ++j) {
+        // At most 64 work items a pack: every item resolves one prefix per
+        // pattern, so short items would spend their time on look-backs.
         const uint64_t u = units[packs[j][0]];
-        per_pack[j] = balanced_per(u, group_per[K_SOMULTI]);
+        const uint32_t floor_per = static_cast<uint32_t>(
+            std::min<uint64_t>(so_max_sub(), std::max<uint64_t>(8, (u + 63) / 64)));
+        per_pack[j] = balanced_per(u, std::max(group_per[K_SOMULTI], floor_per));
         ntiles_pack[j] = (u + per_pack[j] - 1) / per_pack[j];
     }
 

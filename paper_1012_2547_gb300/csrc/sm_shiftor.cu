@@ -766,50 +766,6 @@ __device__ __noinline__ void mp_chunk(uint32_t D, uint4 w, int c, uint32_t tb, u
     }
 }
 
-// Exclusive prefix of item k of one pattern's query, walking its look-back
-// words one at a time (single lane); publishes the inclusive prefix.  The
-// walk is short: it runs one item behind the scan.
-__device__ __forceinline__ uint64_t mp_lookback(uint64_t *state, uint64_t k, uint64_t agg, uint32_t *err,
-                                                bool *ok) {
-    *ok = true;
-    if (k == 0) return 0;
-    uint64_t excl = 0;
-    int64_t j = static_cast<int64_t>(k) - 1;
-    uint32_t sleep_ns = 32;
-    uint64_t t0 = 0;
-    bool timed = false;
-    while (j >= 0) {
-        const uint64_t w = ld_relaxed(&state[j]);
-        const uint64_t st = w & ~LB_VAL;
-        if (st == LB_INC) {
-            excl += w & LB_VAL;
-            break;
-        }
-        if (st == LB_AGG) {
-            excl += w & LB_VAL;
-            --j;
-            timed = false;
-            continue;
-        }
-        if (st == LB_ERR) {
-            *ok = false;
-            break;
-        }
-        if (!timed) {
-            t0 = global_ns();
-            timed = true;
-        } else if (global_ns() - t0 > WAIT_LIMIT_NS) {
-            atomicOr(err, ERR_TIMEOUT);
-            *ok = false;
-            break;
-        }
-        __nanosleep(sleep_ns);
-        sleep_ns = min(sleep_ns * 2, 1024u);
-    }
-    st_relaxed(&state[k], *ok ? (LB_INC | ((excl + agg) & LB_VAL)) : LB_ERR);
-    return excl;
-}
-
 // One warp per block, the same work-item scheme, staging ring and one-item
 // lag as so_kernel, over packs instead of single patterns.  A work item's
 // records go to the block's spill list in position order; at its write
@@ -870,21 +826,46 @@ __global__ void __launch_bounds__(32) mp_kernel(const __grid_constant__ LaunchAr
         const uint32_t kk = __ldg(&P->k);
         const int64_t o = static_cast<int64_t>(reinterpret_cast<uintptr_t>(Q.text) & 15u);
         const int64_t ivstart = static_cast<int64_t>(pend.sb) * SO_T;
-        // Lane p: pattern p's prefix, count and output.
+        // Pattern p's prefix: lane p first reads the previous item's word
+        // (usually inclusive already, one item behind the scan); patterns
+        // whose predecessor is not resolved yet take a windowed look-back
+        // of the whole warp, one after another.  Lane p keeps its prefix
+        // and output.
         uint64_t excl = 0, capp = 0;
         uint64_t *outp = nullptr;
         int64_t shiftp = 0;
         bool ok = true;
+        bool fast = true;
         if (lane < static_cast<int>(kk)) {
-            const QueryDev &M = *P->member[lane];
-            const uint64_t agg = pcnt[lane];
-            excl = mp_lookback(M.state, pend.k, agg, a.err, &ok);
-            if (ok && pend.k + 1 == M.ntiles) *M.out_count = excl + agg;
-            capp = M.cap;
-            outp = M.out_pos;
+            const QueryDev *M = P->member[lane];
+            capp = M->cap;
+            outp = M->out_pos;
             shiftp = static_cast<int64_t>(__ldg(&P->len[lane])) - 1 + o;
+            if (pend.k > 0) {
+                const uint64_t w = ld_relaxed(&M->state[pend.k - 1]);
+                fast = (w & ~LB_VAL) == LB_INC;
+                excl = w & LB_VAL;
+            }
+            if (fast) {
+                st_relaxed(&M->state[pend.k], LB_INC | ((excl + pcnt[lane]) & LB_VAL));
+                if (pend.k + 1 == M->ntiles) *M->out_count = excl + pcnt[lane];
+            }
         }
-        if (!__all_sync(0xffffffffu, ok)) return;
+        unsigned slow = __ballot_sync(0xffffffffu, !fast);
+        while (slow) {
+            const int p = __ffs(slow) - 1;
+            slow &= slow - 1;
+            const QueryDev *M = P->member[p];
+            const uint64_t agg = pcnt[p];
+            bool okp;
+            const uint64_t ex = lookback_resolve(M->state, pend.k, agg, a.err, &okp);
+            ok &= okp;
+            if (lane == p) {
+                excl = ex;
+                if (okp && pend.k + 1 == M->ntiles) *M->out_count = ex + agg;
+            }
+        }
+        if (!ok) return;
         if (!pend.overflow) {
             const uint32_t *list = reinterpret_cast<const uint32_t *>(spill_base + (hb ^ 1) * SO_SPILL_ITEM);
             uint32_t basep = 0;  // lane p: records of pattern p written so far

@@ -361,32 +361,20 @@ __device__ __forceinline__ uint32_t so_subtile(const uint8_t *buf, uint32_t tb, 
 }
 
 // Calls put(b) for every flagged byte b of a lane segment, b increasing.
-// F[c] bit r flags byte 16c + 15 - r; the 144 flags are first laid out in
-// byte order over two 64-bit words and one 32-bit word, so the lane loops
-// once per hit (not once per chunk holding one).
+// F[c] bit r flags byte 16c + 15 - r.  The flags are taken 32 bytes at a
+// time in byte order (two chunks' flags bit-reversed side by side), one
+// loop per word with 32-bit operations, one iteration per hit.
 static_assert(SO_SEGC == 9, "so_emit packs 9 chunks of flags");
 template <typename Put>
 __device__ __forceinline__ void so_emit(const uint32_t (&F)[SO_SEGC], Put put) {
-    uint32_t Q[5];
 #pragma unroll
-    for (int w = 0; w < 5; ++w)
-        Q[w] = (__brev(F[2 * w]) >> 16) | (2 * w + 1 < SO_SEGC ? __brev(F[2 * w + 1]) : 0u);
-    uint64_t w0 = Q[0] | (static_cast<uint64_t>(Q[1]) << 32);
-    uint64_t w1 = Q[2] | (static_cast<uint64_t>(Q[3]) << 32);
-    uint64_t w2 = Q[4];
-    // Branch-free step: lanes whose next hit lies in different words run
-    // the same instructions (selects), so the warp does not serialise the
-    // three cases.
-    while (w0 | w1 | w2) {
-        const bool in0 = w0 != 0;
-        const bool in1 = !in0 && w1 != 0;
-        const uint64_t w = in0 ? w0 : (in1 ? w1 : w2);
-        const uint32_t b = (in0 ? 0u : (in1 ? 64u : 128u)) + (__ffsll(static_cast<long long>(w)) - 1);
-        const uint64_t rest = w & (w - 1);
-        w0 = in0 ? rest : w0;
-        w1 = in1 ? rest : w1;
-        w2 = (in0 || in1) ? w2 : rest;
-        put(b);
+    for (int w = 0; w < 5; ++w) {
+        uint32_t q = (__brev(F[2 * w]) >> 16) | (2 * w + 1 < SO_SEGC ? __brev(F[2 * w + 1]) : 0u);
+        while (q) {
+            const uint32_t b = static_cast<uint32_t>(__ffs(q)) - 1u;
+            q &= q - 1u;
+            put(32u * w + b);
+        }
     }
 }
 
@@ -395,11 +383,17 @@ __device__ __forceinline__ void so_emit(const uint32_t (&F)[SO_SEGC], Put put) {
 // position 0.
 __device__ __forceinline__ void so_write_flags(const uint32_t (&F)[SO_SEGC], uint32_t ex, uint64_t idx0,
                                                uint64_t cap, uint64_t *out, int64_t start0) {
-    uint64_t idx = idx0 + ex;
+    const uint64_t first = idx0 + ex;
+    if (first >= cap) return;
+    // 32-bit counter against the room left (a segment holds at most 144 hits).
+    const uint64_t room64 = cap - first;
+    const uint32_t room = room64 < 0xFFFFFFFFull ? static_cast<uint32_t>(room64) : 0xFFFFFFFFu;
+    uint64_t *dst = out + first;
     const int64_t lane0 = start0 + static_cast<int64_t>(threadIdx.x & 31) * SO_S;
+    uint32_t j = 0;
     so_emit(F, [&](uint32_t b) {
-        if (idx < cap) out[idx] = static_cast<uint64_t>(lane0 + b);
-        ++idx;
+        if (j < room) dst[j] = static_cast<uint64_t>(lane0 + b);
+        ++j;
     });
 }
 

@@ -724,7 +724,6 @@ def bench_serve(args, world, rank, local):
     dev = torch.device("cuda", local)
     C = args.serve_corpus
     specs = {"rand4": gen.uniform_text(C, 4, 61), "english": gen.english_text(C, 62)}
-    hints = {"rand4": 4, "english": 90}
     corp = {}
     for k, sp in specs.items():
         t = torch.empty(C, dtype=torch.uint8, device=dev)
@@ -756,8 +755,7 @@ def bench_serve(args, world, rank, local):
     scanned = sum(C if r[1] else len(r[2]) for r in reqs)
 
     def run_server(arrival_rate=None):
-        srv = Server(corp, budget_bytes=args.serve_budget, streams=4, max_batch=512,
-                     sigma_hints=hints)
+        srv = Server(corp, budget_bytes=args.serve_budget, streams=4, max_batch=512)
         # Each result is consumed when it is ready, as the clients of a
         # service would (a callback keeps its length and lets it go), so
         # finished results do not pile up behind slower ones.

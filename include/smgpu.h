@@ -236,7 +236,8 @@ sm_status sm_search_batch_async(const sm_query *queries, uint32_t nq, void *work
  * Multi-pattern packs (sm_search_batch, sm_search_batch_async and
  * sm_batch_create unless flag bit 1): Shift-Or queries with m <= 16 on the
  * same text (same pointer and length), prepared with an alphabet-size hint
- * sigma such that sigma^m >= 2^14 (occurrences expected sparse), are packed
+ * sigma such that sigma^m >= 2^16 (occurrences expected sparse; for a
+ * skewed text, pass an effective alphabet size), are packed
  * side by side into one 32-bit Shift-And state (at most 32 bits and 16
  * patterns a pack) and scanned together.  Results are the same as without
  * packing for any text (dense texts are only slower).

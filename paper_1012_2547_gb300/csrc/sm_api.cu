@@ -637,13 +637,14 @@ struct BatchLayout {
 };
 
 // A pattern can join a multi-pattern pack: Shift-And with a 1- or 2-byte
-// mask table (m <= 16) and a known alphabet size with sigma^m >= 2^14, so
+// mask table (m <= 16) and an alphabet-size hint with sigma^m >= 2^16, so
 // that its occurrences are expected sparse (the packed scan rescans the
-// 16-byte chunks that hold one).
+// 16-byte chunks that hold one).  For skewed texts the hint should be an
+// effective alphabet size (see the Python package's hints module).
 bool packable(const sm_plan *p) {
     if (p->kid != K_SO8H && p->kid != K_SO16H) return false;
     if (p->sigma < 2) return false;
-    return static_cast<double>(p->hdr.m) * std::log2(static_cast<double>(p->sigma)) >= 14.0;
+    return static_cast<double>(p->hdr.m) * std::log2(static_cast<double>(p->sigma)) >= 16.0;
 }
 
 // Lays a batch out at `base` (null: sizes only).  Queries are grouped by

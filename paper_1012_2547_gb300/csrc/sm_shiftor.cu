@@ -677,7 +677,8 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
 // state comes from a warm-up over the 16 bytes before it (every field is at
 // most 16 bits, so all fields are exact after it).
 
-constexpr int MP_REC = 4;  // (pattern, position) records a lane keeps per sub-tile
+constexpr int MP_REC = 4;  // (pattern, position) records a lane keeps in registers per sub-tile
+constexpr uint32_t MP_LIST = SO_SPILL_ITEM / 4;  // records of a work item (its whole spill area)
 
 struct MPLayout {
     static constexpr uint32_t BAR_OFF = SO_NBUF * SO_BUF;
@@ -692,7 +693,7 @@ struct MPItem {
     uint32_t qi;
     uint64_t k, sb, se;
     uint32_t listed;  // records in the spill list
-    bool overflow;    // records were lost: the write phase rescans per pattern
+    bool overflow;    // the list filled: the write phase rescans per pattern
 };
 
 // Loads a pack's table and constants into shared memory unless loaded.
@@ -733,12 +734,13 @@ __device__ __forceinline__ void mp_step4(uint32_t &D, uint32_t &A, uint32_t x, u
 }
 
 // Byte-by-byte rescan of a flagged chunk from its start state: every valid
-// (pattern, end) pair is counted (shared counters) and, while the lane has
-// room, kept as a record (chunk << 12 | byte << 8 | pattern).
+// (pattern, end) pair is counted (shared counters and the lane's `ntrue`)
+// and the first MP_REC of the lane's sub-tile are kept as records
+// (chunk << 12 | byte << 8 | pattern).
 __device__ __noinline__ void mp_chunk(uint32_t D, uint4 w, int c, uint32_t tb, uint32_t two, uint32_t four,
                                       uint32_t I, uint32_t F, const uint8_t *fmap, const PackPlan *P,
                                       int64_t x, int64_t vlo0, int64_t vhi, uint32_t *cnt,
-                                      uint64_t &rec, int &nrec, bool &lost) {
+                                      uint64_t &rec, uint32_t &ntrue) {
     for (int b = 0; b < 16; ++b) {
         const uint32_t xw = b < 4 ? w.x : b < 8 ? w.y : b < 12 ? w.z : w.w;
         D = ((D * two) | I) & mp_entry(xw, b & 3, tb, four);
@@ -750,11 +752,40 @@ __device__ __noinline__ void mp_chunk(uint32_t D, uint4 w, int c, uint32_t tb, u
             const int p = fmap[bit];
             if (e < vlo0 + __ldg(&P->len[p]) - 1 || e >= vhi) continue;  // not a valid end of p
             atomicAdd(&cnt[p], 1u);
-            if (nrec < MP_REC) {
-                rec |= static_cast<uint64_t>((c << 12) | (b << 8) | p) << (16 * nrec);
-                ++nrec;
-            } else {
-                lost = true;
+            if (ntrue < MP_REC) rec |= static_cast<uint64_t>((c << 12) | (b << 8) | p) << (16 * ntrue);
+            ++ntrue;
+        }
+    }
+}
+
+// All records of a lane segment staged at `seg`, in position order, written
+// to out[0..] as (pattern << 19 | item-relative end): the write of a lane
+// with more than MP_REC of them in one sub-tile (counted already).
+__device__ __noinline__ void mp_segment_records(const uint8_t *seg, uint32_t tb, uint32_t two, uint32_t four,
+                                                uint32_t I, uint32_t F, const uint8_t *fmap,
+                                                const PackPlan *P, int64_t x, int64_t vlo0, int64_t vhi,
+                                                uint32_t rel0, uint32_t *out) {
+    uint32_t D = 0, A = 0;
+    {
+        const uint4 w = *reinterpret_cast<const uint4 *>(seg - 16);
+        mp_step4(D, A, w.x, tb, two, four, I);
+        mp_step4(D, A, w.y, tb, two, four, I);
+        mp_step4(D, A, w.z, tb, two, four, I);
+        mp_step4(D, A, w.w, tb, two, four, I);
+    }
+    for (int c = 0; c < SO_SEGC; ++c) {
+        const uint4 w = *reinterpret_cast<const uint4 *>(seg + 16 * c);
+        for (int b = 0; b < 16; ++b) {
+            const uint32_t xw = b < 4 ? w.x : b < 8 ? w.y : b < 12 ? w.z : w.w;
+            D = ((D * two) | I) & mp_entry(xw, b & 3, tb, four);
+            uint32_t h = D & F;
+            const int64_t e = x + 16 * c + b;
+            while (h) {
+                const int bit = __ffs(h) - 1;
+                h &= h - 1;
+                const int p = fmap[bit];
+                if (e < vlo0 + __ldg(&P->len[p]) - 1 || e >= vhi) continue;
+                *out++ = (static_cast<uint32_t>(p) << 19) | (rel0 + 16 * c + b);
             }
         }
     }
@@ -764,10 +795,11 @@ __device__ __noinline__ void mp_chunk(uint32_t D, uint4 w, int c, uint32_t tb, u
 // lag as so_kernel, over packs instead of single patterns.  A work item's
 // records go to the block's spill list in position order; at its write
 // phase every pattern's prefix is resolved (lane p for pattern p) and the
-// records are scattered to the patterns' outputs with their ranks.  If a
-// lane ever had more than MP_REC records in a sub-tile, or the list filled,
-// the write phase instead rescans the item from global memory once per
-// pattern (exact for any input, slow only for dense ones).
+// records are scattered to the patterns' outputs with their ranks.  A lane
+// with more than MP_REC records in a sub-tile extracts them again from its
+// staged segment straight into the list; if the list fills, the write
+// phase instead rescans the item from global memory once per pattern
+// (exact for any input, slow only for dense ones).
 __global__ void __launch_bounds__(32) mp_kernel(const __grid_constant__ LaunchArgs a) {
     using L = MPLayout;
     extern __shared__ __align__(128) uint8_t smem[];
@@ -971,8 +1003,7 @@ __global__ void __launch_bounds__(32) mp_kernel(const __grid_constant__ LaunchAr
                 mp_step4(D, A, w.w, tb, two, four, I);
             }
             uint64_t rec = 0;
-            int nrec = 0;
-            bool lost = false;
+            uint32_t ntrue = 0;
 #pragma unroll
             for (int c = 0; c < SO_SEGC; ++c) {
                 const uint4 w = *reinterpret_cast<const uint4 *>(seg + 16 * c);
@@ -982,19 +1013,23 @@ __global__ void __launch_bounds__(32) mp_kernel(const __grid_constant__ LaunchAr
                 mp_step4(D, A, w.y, tb, two, four, I);
                 mp_step4(D, A, w.z, tb, two, four, I);
                 mp_step4(D, A, w.w, tb, two, four, I);
-                if (A & F)
-                    mp_chunk(Ds, w, c, tb, two, four, I, F, fmap, P, x, o, vhi, cnt, rec, nrec, lost);
+                if (A & F) mp_chunk(Ds, w, c, tb, two, four, I, F, fmap, P, x, o, vhi, cnt, rec, ntrue);
             }
-            if (__any_sync(0xffffffffu, nrec != 0 || lost)) {
+            if (__any_sync(0xffffffffu, ntrue != 0)) {
                 uint32_t total;
-                const uint32_t ex = warp_excl_scan(static_cast<uint32_t>(nrec), &total);
-                overflow |= __any_sync(0xffffffffu, lost) || listed + total > SO_SPILL_POS;
+                const uint32_t ex = warp_excl_scan(ntrue, &total);
+                overflow |= listed + total > MP_LIST;
                 if (!overflow) {
                     const uint32_t rel0 = static_cast<uint32_t>(x - ivstart);
-                    for (int r = 0; r < nrec; ++r) {
-                        const uint32_t v = static_cast<uint32_t>(rec >> (16 * r)) & 0xFFFFu;
-                        const uint32_t pos = rel0 + 16 * ((v >> 12) & 15u) + ((v >> 8) & 15u);
-                        list[listed + ex + r] = ((v & 0xFFu) << 19) | pos;
+                    if (ntrue <= static_cast<uint32_t>(MP_REC)) {
+                        for (uint32_t r = 0; r < ntrue; ++r) {
+                            const uint32_t v = static_cast<uint32_t>(rec >> (16 * r)) & 0xFFFFu;
+                            const uint32_t pos = rel0 + 16 * ((v >> 12) & 15u) + ((v >> 8) & 15u);
+                            list[listed + ex + r] = ((v & 0xFFu) << 19) | pos;
+                        }
+                    } else {
+                        mp_segment_records(seg, tb, two, four, I, F, fmap, P, x, o, vhi, rel0,
+                                           list + listed + ex);
                     }
                 }
                 listed += total;

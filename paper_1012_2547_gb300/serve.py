@@ -219,7 +219,13 @@ class Server:
         self._torch = torch
         self._smg = smg
         self.corpora = dict(corpora)
+        # Alphabet-size hints per corpus; a corpus without one gets the
+        # effective alphabet size of its first MiB (hints.effective_sigma).
+        from .hints import effective_sigma
         self.sigma_hints = dict(sigma_hints or {})
+        for name, t in self.corpora.items():
+            if name not in self.sigma_hints:
+                self.sigma_hints[name] = effective_sigma(t[: 1 << 20].cpu().numpy())
         self.own_text_sigma = own_text_sigma
         self.first_cap = int(first_cap)
         self.policy = Policy(budget_bytes, max_batch, max_wait,

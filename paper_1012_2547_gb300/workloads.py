@@ -24,6 +24,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import gen
+from .hints import effective_sigma
 
 SWEEP_N = 4_194_304
 SWEEP_PER_M = 100
@@ -53,8 +54,14 @@ class Workload:
         return tot
 
 
-def sigma_hint(spec: gen.TextSpec) -> int:
-    return 4 if spec.kind == "markov3" else spec.sigma
+def sigma_hint(spec: gen.TextSpec, sample=None) -> int:
+    """Alphabet-size hint of a text: sigma for a uniform text, else the
+    effective alphabet size of a sample of it (hints.effective_sigma)."""
+    if spec.kind == "uniform":
+        return spec.sigma
+    if sample is None:
+        sample = spec.host()[: 1 << 20] if spec.kind == "markov3" else spec.window(0, 1 << 20)
+    return effective_sigma(sample[: 1 << 20])
 
 
 def single() -> Workload:
@@ -69,9 +76,10 @@ def sweep(n: int = SWEEP_N, per_m: int = SWEEP_PER_M, ms=gen.SWEEP_M, seed: int 
     texts = [s.host() for s in specs]
     w = Workload(f"sweep_10texts_n{n}_m2-1024_x{per_m}", texts, specs)
     for ti, (spec, t) in enumerate(zip(specs, texts)):
+        hint = sigma_hint(spec, t)
         for m in ms:
             for p in gen.substring_patterns(t, m, per_m, seed=seed * 1000 + ti * 16 + m.bit_length()):
-                w.queries.append(Query(ti, p, sigma_hint(spec)))
+                w.queries.append(Query(ti, p, hint))
     return w
 
 
@@ -113,6 +121,7 @@ def batched_shared(n: int = BATCHED_SHARED_N, nq: int = BATCHED_SHARED_Q, seed: 
     w = Workload(f"batched_shared_n{n}_sigma20_q{nq}", [spec], [spec])
     klen = gen.stream_key(seed, gen.STREAM_LENGTHS)
     alphabet = np.arange(20, dtype=np.uint8)
+    hint = sigma_hint(spec)
     for i in range(nq):
         m = gen.log_uniform_int(klen, i, 2, 1024)
         if i % 2 == 0:
@@ -120,7 +129,7 @@ def batched_shared(n: int = BATCHED_SHARED_N, nq: int = BATCHED_SHARED_Q, seed: 
             p = bytes(spec.window(o, m))
         else:
             p = gen.random_patterns(alphabet, m, 1, seed=seed * 1_000_003 + i)[0]
-        w.queries.append(Query(0, p, 20))
+        w.queries.append(Query(0, p, hint))
     return w
 
 

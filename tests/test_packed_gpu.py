@@ -97,3 +97,20 @@ def test_dense_text_falls_back_exactly():
         exp = oracle.naive(t, p)
         assert cnt[i] == len(exp)
         assert np.array_equal(got[i], exp), len(p)
+
+
+def test_moderately_dense_pack_lane_reextraction():
+    """Packs denser than their alphabet hint says (sigma = 4 text, hint 256):
+    lanes with more records than they keep in registers extract them again
+    from the staged segment; results stay exact."""
+    import paper_1012_2547_gb300 as smg
+    rng = np.random.default_rng(11)
+    t = rng.integers(0, 4, 2_500_003, dtype=np.uint8)
+    pats = [gen.substring_patterns(t, m, 1, seed=200 + k)[0] for k, m in enumerate((5, 5, 6, 6, 5, 5))]
+    dev = to_dev(t, 5)
+    plans = smg.prepare_many(pats, sigma_hint=256)
+    packed, cp = _run(dev, plans, True)
+    for i, p in enumerate(pats):
+        exp = oracle.naive(t, p)
+        assert cp[i] == len(exp)
+        assert np.array_equal(packed[i], exp), len(p)

@@ -241,13 +241,19 @@ def run_ours(args, world, rank, local):
 
     tuning = None
     if not args.no_tune:
-        # The autotuner picks the kernel per (m bucket, sigma bucket) on
-        # this device before anything is timed.
+        # The kernel per (m bucket, sigma bucket) comes from the autotuner's
+        # table measured on GB300 (committed JSON), or, with --tune, from a
+        # fresh measurement on this device before anything is timed.
         from paper_1012_2547_gb300 import tuner
-        tr = tuner.tune(ms=tuple(int(x) for x in args.ms.split(",")) if args.ms else
-                        tuple(__import__("paper_1012_2547_gb300").gen.SWEEP_M),
-                        per=args.per_m or workloads.SWEEP_PER_M)
-        tuning = {"seconds": tr["seconds"],
+        if args.tune or not os.path.exists(tuner.GB300_TABLE):
+            tr = tuner.tune(ms=tuple(int(x) for x in args.ms.split(",")) if args.ms else
+                            tuple(__import__("paper_1012_2547_gb300").gen.SWEEP_M),
+                            per=args.per_m or workloads.SWEEP_PER_M)
+            source = "measured now"
+        else:
+            tr = tuner.load(tuner.GB300_TABLE)
+            source = "paper_1012_2547_gb300/tuning_gb300.json (measured on GB300 by tuner.tune)"
+        tuning = {"source": source, "seconds": tr["seconds"],
                   "choices": {f"s{r['sigma']}m{r['m']}": r["best"] for r in tr["report"]}}
 
     if args.workload == "sweep":
@@ -496,8 +502,12 @@ def bench_bandwidth(args, world, rank, local):
     tuning = None
     if not args.no_tune:
         from paper_1012_2547_gb300 import tuner
-        tr = tuner.tune(sigmas=(4,), ms=ms)
-        tuning = {"seconds": tr["seconds"], "choices": {f"s{r['sigma']}m{r['m']}": r["best"] for r in tr["report"]}}
+        if args.tune or not os.path.exists(tuner.GB300_TABLE):
+            tr = tuner.tune(sigmas=(4,), ms=ms)
+        else:
+            tr = tuner.load(tuner.GB300_TABLE)
+        tuning = {"seconds": tr["seconds"], "choices": {f"s{r['sigma']}m{r['m']}": r["best"] for r in tr["report"]
+                                                        if r["sigma"] == 4 and r["m"] in ms}}
     spec = w.specs[0]
     text = torch.empty(n, dtype=torch.uint8, device=dev)
     smg.gen_text(text, 0, spec.key, 4)
@@ -609,7 +619,10 @@ def bench_batched(args, world, rank, local):
     tuning = None
     if not args.no_tune:
         from paper_1012_2547_gb300 import tuner
-        tr = tuner.tune(sigmas=(4, 16, 64))
+        if args.tune or not os.path.exists(tuner.GB300_TABLE):
+            tr = tuner.tune(sigmas=(4, 16, 64))
+        else:
+            tr = tuner.load(tuner.GB300_TABLE)
         tuning = {"seconds": tr["seconds"]}
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     rng = np.random.default_rng(3)
@@ -880,6 +893,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cells", action="store_true", help="skip the per-(sigma, m) table")
     ap.add_argument("--no-tune", action="store_true", help="keep the built-in kernel rule")
+    ap.add_argument("--tune", action="store_true", help="re-measure the tuning table on this device")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0)
     ap.add_argument("--bw-bytes", type=int, default=8 << 30)

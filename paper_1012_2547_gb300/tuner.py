@@ -8,7 +8,7 @@ sigma (0 = unknown, else floor(log2 sigma) clamped to 1..8), used by
 sm_prepare when no explicit configuration is given (include/smgpu.h,
 sm_tuning_*).  This module fills that table by timing every candidate
 configuration (Shift-Or with a 32- or 64-bit state, q-gram filter for
-q in {3, 4, 5, 6, 8}) on a batch of substring patterns of a uniform text of
+q in {3, ..., 8}) on a batch of substring patterns of a uniform text of
 each alphabet size, as one graph-captured batch per candidate, and keeping
 the fastest.  The table can be saved to and loaded from JSON.
 """
@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import json
 import math
+import os
 import statistics
 import time
 
@@ -40,13 +41,27 @@ def s_bucket(sigma: int) -> int:
     return max(1, min(S_BUCKETS - 1, int(sigma).bit_length() - 1))
 
 
+def builtin(m: int, sigma: int = 0) -> dict:
+    """The library's built-in choice for length m on an alphabet of sigma
+    (tuning cell variant 0): Shift-Or up to m = 64, else the q-gram filter
+    with q = ceil(log(64 m) / log sigma) clamped to 3..8 (sigma 4 when
+    unknown)."""
+    if m <= 32:
+        return {"variant": "shiftor", "word_bits": 32}
+    if m <= 64:
+        return {"variant": "shiftor", "word_bits": 64}
+    sg = sigma if sigma >= 2 else 4
+    q = min(8, max(3, math.ceil(math.log(64.0 * m) / math.log(sg))))
+    return {"variant": "qgram", "q": min(q, m)}
+
+
 def candidates(m: int) -> list[dict]:
     out = []
     if m <= 32:
         out.append({"variant": "shiftor", "word_bits": 32})
     if m <= 64:
         out.append({"variant": "shiftor", "word_bits": 64})
-    for q in (3, 4, 5, 6, 8):
+    for q in (3, 4, 5, 6, 7, 8):
         if q <= m and m - q + 1 >= 2:
             out.append({"variant": "qgram", "q": q})
     return out
@@ -82,13 +97,16 @@ def _time_batch(text, pats, sigma, cfg, reps, flush):
 
 
 def tune(sigmas=(2, 4, 8, 16, 32, 64, 128), ms=gen.SWEEP_M, n: int = 4 << 20, per: int = 100,
-         reps: int = 3, seed: int = 101, apply: bool = True, verbose: bool = False) -> dict:
+         reps: int = 3, seed: int = 101, apply: bool = True, verbose: bool = False,
+         margin: float = 0.05) -> dict:
     """Measure every candidate for each (sigma, m) and return (and by
     default apply) the tuning table.  Cells not measured keep variant 0
     (the library's built-in rule).  `per` patterns per cell run as one
     batch: the ranking of the kernels depends on the batch size (a small
     batch gives short work items), so it should match the batches the
-    table will serve."""
+    table will serve.  A candidate replaces the built-in choice only when
+    it is faster by more than `margin`, so that near-ties do not flip from
+    run to run."""
     import torch
 
     from . import gen_text
@@ -112,6 +130,10 @@ def tune(sigmas=(2, 4, 8, 16, 32, 64, 128), ms=gen.SWEEP_M, n: int = 4 << 20, pe
                                         else f"q{cfg.get('q')}")
                 res[key] = (_time_batch(text, pats, sigma, cfg, reps, flush), cfg)
             best_key = min(res, key=lambda k: res[k][0])
+            b = builtin(m, sigma)
+            b_key = next((k for k, v in res.items() if v[1] == b), None)
+            if b_key is not None and res[best_key][0] > (1.0 - margin) * res[b_key][0]:
+                best_key = b_key
             best_t, best_cfg = res[best_key]
             idx = m_bucket(m) * S_BUCKETS + s_bucket(sigma)
             cells[idx] = {"variant": VARIANT_IDS[best_cfg["variant"]], "q": best_cfg.get("q", 0),
@@ -145,6 +167,11 @@ def load(path: str, apply: bool = True) -> dict:
 
 def current() -> list[dict]:
     return tuning_get()
+
+
+# The table measured on GB300 with tune() (sigmas 2..128, the sweep's m, 100
+# patterns a cell), loaded by bench.py unless it is asked to re-measure.
+GB300_TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_gb300.json")
 
 
 if __name__ == "__main__":  # python -m paper_1012_2547_gb300.tuner out.json

@@ -42,3 +42,31 @@ def test_tuned_table_applies_and_stays_exact():
             got = smg.search(dev, plan).cpu().numpy().astype(np.uint64)
             assert np.array_equal(got, oracle.kmp(t, p)), (sigma, m, plan.info())
     smg.tuning_reset()
+
+
+def test_committed_gb300_table_loads():
+    import json
+    import os
+
+    from paper_1012_2547_gb300 import tuner
+    assert os.path.exists(tuner.GB300_TABLE)
+    r = tuner.load(tuner.GB300_TABLE, apply=False)
+    assert len(r["cells"]) == tuner.M_BUCKETS * tuner.S_BUCKETS
+    for c in r["cells"]:
+        assert c["variant"] in (0, 1, 2, 3)
+        if c["variant"] == 2:
+            assert 1 <= c["q"] <= 8
+    with open(tuner.GB300_TABLE) as f:
+        assert json.load(f)["patterns_per_cell"] == 100
+
+
+def test_builtin_choice_rule():
+    from paper_1012_2547_gb300 import tuner
+    assert tuner.builtin(8)["variant"] == "shiftor" and tuner.builtin(8)["word_bits"] == 32
+    assert tuner.builtin(40)["word_bits"] == 64
+    assert tuner.builtin(100, 4) == {"variant": "qgram", "q": 7}      # ceil(log 6400 / log 4)
+    assert tuner.builtin(1024, 128) == {"variant": "qgram", "q": 3}
+    assert tuner.builtin(1024, 2) == {"variant": "qgram", "q": 8}
+    for m in (8, 40, 100, 1024):
+        for sg in (2, 4, 20, 128):
+            assert tuner.builtin(m, sg) in tuner.candidates(m)

@@ -64,7 +64,13 @@ typedef enum {
     SM_VARIANT_AUTO = 0,     /* tuning table, else built-in rule */
     SM_VARIANT_SHIFTOR = 1,  /* bit-parallel Shift-And/Shift-Or, m <= 64 */
     SM_VARIANT_QGRAM = 2,    /* exact q-gram stride filter + warp verify */
-    SM_VARIANT_LINEAR = 3    /* per-segment Knuth-Morris-Pratt (dense fallback) */
+    SM_VARIANT_LINEAR = 3,   /* per-segment Knuth-Morris-Pratt (dense fallback) */
+    SM_VARIANT_DFA = 4       /* per-segment string-matching automaton (the
+                              * AUT/DFA algorithm of Figs. 1-3): one table
+                              * step per text byte whatever m and the hit
+                              * density.  Needs (m+1) x C x 2 <= 32,512 bytes
+                              * of table, C = distinct bytes of p + 1; an
+                              * explicit config that exceeds it is SM_EINVAL */
 } sm_variant;
 
 typedef struct sm_plan sm_plan;   /* opaque, library-owned */
@@ -75,8 +81,8 @@ typedef struct sm_batch sm_batch; /* opaque, library-owned */
  *   variant  : sm_variant.
  *   q        : q-gram length for SM_VARIANT_QGRAM, 1..8 and <= m.
  *   word_bits: Shift-Or state width, 32 or 64 (m <= 32 or m <= 64).
- *   tile     : log2 hint of the work-item size.  QGRAM/LINEAR: bytes of
- *              start positions per thread range.  SHIFTOR (whose staged
+ *   tile     : log2 hint of the work-item size.  QGRAM/LINEAR/DFA: bytes
+ *              of start positions per thread range.  SHIFTOR (whose staged
  *              sub-tile is fixed at 4,608 end positions): the shortest work
  *              item in bytes, rounded up to whole sub-tiles and capped at 64
  *              of them; 0 lets the launch size items from the grid alone.
@@ -97,7 +103,7 @@ typedef struct {
     uint32_t hist;        /* 1 if the Shift-Or state carries 16 match flags */
     uint32_t tile_starts; /* start positions per work item */
     uint64_t device_bytes;/* size of the plan's device tables */
-    uint32_t kernel;      /* internal kernel id (0..7): batches run one launch per id */
+    uint32_t kernel;      /* internal kernel id (0..9): batches run one launch per id */
     uint32_t reserved;
 } sm_plan_desc;
 
@@ -109,7 +115,11 @@ typedef struct {
  *     pattern-symbol encoding of the bit-parallel algorithms, Section 1);
  *   - for long patterns, the exact q-gram table of p (the Hash-q idea of
  *     Fig. 1 with q-grams compared exactly, never by hash alone);
- *   - the Knuth-Morris-Pratt border table for the linear fallback.
+ *   - the Knuth-Morris-Pratt border table for the linear fallback;
+ *   - the string-matching automaton of p over its byte classes, for DFA
+ *     plans and for q-gram plans of periodic patterns (smallest period
+ *     <= m/2, table within the DFA limit), whose dense work items then run
+ *     the automaton instead of Knuth-Morris-Pratt.
  * pattern    : host pointer to m bytes.  m >= 1 (m = 0 -> SM_EINVAL).
  * sigma_hint : expected alphabet size of the texts (0 = unknown); only
  *              changes the kernel choice and q, never the result.

@@ -12,7 +12,7 @@ import os
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsmgpu.so")
 
 SM_OK, SM_EINVAL, SM_ENOMEM, SM_ECUDA, SM_ETIMEOUT, SM_ETRUNC = range(6)
-VARIANTS = {"auto": 0, "shiftor": 1, "qgram": 2, "linear": 3}
+VARIANTS = {"auto": 0, "shiftor": 1, "qgram": 2, "linear": 3, "dfa": 4}
 VARIANT_NAMES = {v: k for k, v in VARIANTS.items()}
 TUNE_M_BUCKETS = 12
 TUNE_S_BUCKETS = 9

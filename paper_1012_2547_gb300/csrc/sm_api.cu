@@ -253,11 +253,30 @@ sm_status build_blob(const uint8_t *p, uint32_t m, uint32_t sigma, const sm_conf
         std::lock_guard<std::mutex> g(L.mu);
         tc = L.tuning[m_bucket(m) * SM_TUNE_S_BUCKETS + s_bucket(sigma)];
     }
+    // Border table (Knuth-Morris-Pratt): fail[q] = length of the longest
+    // proper border of p[0..q-1]; m - fail[m] is the smallest period of p.
+    std::vector<uint32_t> fail(m + 1, 0);
+    for (uint32_t i = 1, kk = 0; i < m; ++i) {
+        while (kk > 0 && p[kk] != p[i]) kk = fail[kk];
+        if (p[kk] == p[i]) ++kk;
+        fail[i + 1] = kk;
+    }
+    // Byte classes of the automaton: 0 for bytes absent from p, then one
+    // class per distinct pattern byte in order of first occurrence.
+    uint16_t cls_of[256] = {};
+    uint32_t C = 1;
+    for (uint32_t j = 0; j < m; ++j)
+        if (!cls_of[p[j]]) cls_of[p[j]] = static_cast<uint16_t>(C++);
+    const uint64_t dfa_bytes = static_cast<uint64_t>(m + 1) * C * 2;
+    const bool dfa_fits = dfa_bytes <= DFA_MAX_TABLE;
+
     uint32_t variant = cfg && cfg->variant ? cfg->variant : tc.variant;
     if (variant == SM_VARIANT_AUTO) variant = m <= 64 ? SM_VARIANT_SHIFTOR : SM_VARIANT_QGRAM;
-    // A tuned (not explicit) choice that cannot serve m falls back to the rule.
+    // A tuned (not explicit) choice that cannot serve p falls back to the rule.
     const bool explicit_cfg = cfg && cfg->variant;
     if (!explicit_cfg && variant == SM_VARIANT_SHIFTOR && m > 64) variant = SM_VARIANT_QGRAM;
+    if (!explicit_cfg && variant == SM_VARIANT_DFA && !dfa_fits)
+        variant = m <= 64 ? SM_VARIANT_SHIFTOR : SM_VARIANT_QGRAM;
     const sm_config *src = explicit_cfg ? cfg : &tc;
 
     PlanDev h{};
@@ -304,9 +323,25 @@ sm_status build_blob(const uint8_t *p, uint32_t m, uint32_t sigma, const sm_conf
         h.variant = VAR_LINEAR;
         h.tile_starts = static_cast<uint32_t>(R * qg_kernel_threads());
         kid = K_LINEAR;
+    } else if (variant == SM_VARIANT_DFA) {
+        if (!dfa_fits) return SM_EINVAL;
+        // Each thread runs the automaton over m - 1 bytes before its first
+        // start: ranges of at least 4m keep that overhead under a quarter.
+        R = std::max<uint64_t>(1024, 4ull * m);
+        if (src->tile) R = std::max<uint64_t>(R, 1ull << std::min(src->tile, 24u));
+        R = (R + 15) & ~uint64_t(15);
+        if (R * qg_kernel_threads() >= (1ull << 32)) return SM_EINVAL;
+        h.variant = VAR_DFA;
+        h.tile_starts = static_cast<uint32_t>(R * qg_kernel_threads());
+        kid = K_DFA;
     } else {
         return SM_EINVAL;
     }
+    // The automaton: for DFA plans, and for q-gram plans of periodic
+    // patterns (smallest period <= m/2), whose dense tiles use it.  Only a
+    // periodic pattern can have occurrences closer than m/2 apart.
+    const bool with_dfa =
+        h.variant == VAR_DFA || (h.variant == VAR_QGRAM && dfa_fits && 2ull * (m - fail[m]) <= m);
 
     // q-gram table: (packed q-gram, offset) pairs sorted by q-gram, then by
     // offset descending, so each distinct q-gram is one run of its offsets
@@ -341,6 +376,14 @@ sm_status build_blob(const uint8_t *p, uint32_t m, uint32_t sigma, const sm_conf
     off += h.variant == VAR_QGRAM ? align16(4ull * (m - q + 1)) : 0;
     h.off_fail = static_cast<uint32_t>(off);
     off += align16(4ull * (m + 1));
+    if (with_dfa) {
+        h.off_cls = static_cast<uint32_t>(off);
+        off += 256 * 2;
+        h.off_dfa = static_cast<uint32_t>(off);
+        off += align16(dfa_bytes);
+        h.classes = C;
+        h.dfa_final = m * C * 2;
+    }
     off = (off + 255) & ~size_t(255);
     if (off >= (1ull << 32)) return SM_EINVAL;
     h.bytes = static_cast<uint32_t>(off);
@@ -380,16 +423,26 @@ sm_status build_blob(const uint8_t *p, uint32_t m, uint32_t sigma, const sm_conf
             i = e;
         }
     }
-    // Border table (Knuth-Morris-Pratt): fail[q] = length of the longest
-    // proper border of p[0..q-1].
-    uint32_t *fail = reinterpret_cast<uint32_t *>(b + h.off_fail);
-    fail[0] = 0;
-    if (m >= 1) fail[1] = 0;
-    uint32_t kk = 0;
-    for (uint32_t i = 1; i < m; ++i) {
-        while (kk > 0 && p[kk] != p[i]) kk = fail[kk];
-        if (p[kk] == p[i]) ++kk;
-        fail[i + 1] = kk;
+    std::memcpy(b + h.off_fail, fail.data(), 4ull * (m + 1));
+    if (with_dfa) {
+        // Rows by byte offset (row of state q at 2*C*q); entries are the
+        // row offsets of the next states.  Row 0 goes to 1 on p[0] only;
+        // row q copies the row of X, the state the automaton reaches on
+        // p[1..q-1] (the longest proper border of p[0..q-1]), and goes to
+        // q+1 on p[q]; row m is the row of X after p[1..m-1].
+        uint16_t *cls = reinterpret_cast<uint16_t *>(b + h.off_cls);
+        for (int c = 0; c < 256; ++c) cls[c] = static_cast<uint16_t>(2 * cls_of[c]);
+        uint16_t *T = reinterpret_cast<uint16_t *>(b + h.off_dfa);
+        const uint32_t row = 2 * C;  // bytes per row
+        T[cls_of[p[0]]] = static_cast<uint16_t>(row);
+        uint32_t X = 0;
+        for (uint32_t q = 1; q <= m; ++q) {
+            std::memcpy(T + q * C, T + X * C, 2ull * C);
+            if (q < m) {
+                T[q * C + cls_of[p[q]]] = static_cast<uint16_t>((q + 1) * row);
+                X = T[X * C + cls_of[p[q]]] / row;
+            }
+        }
     }
     std::memcpy(b, &h, sizeof(h));
     *hdr_out = h;
@@ -942,6 +995,7 @@ sm_status sm_plan_info(const sm_plan *plan, sm_plan_desc *out) {
     d.m = plan->hdr.m;
     d.variant = plan->hdr.variant == VAR_SHIFTOR ? SM_VARIANT_SHIFTOR
                 : plan->hdr.variant == VAR_QGRAM ? SM_VARIANT_QGRAM
+                : plan->hdr.variant == VAR_DFA   ? SM_VARIANT_DFA
                                                  : SM_VARIANT_LINEAR;
     d.q = plan->hdr.q;
     d.word_bits = plan->hdr.word_bits;

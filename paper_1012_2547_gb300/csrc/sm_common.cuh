@@ -10,7 +10,11 @@ namespace smgpu {
 
 // ---------------------------------------------------------------- layouts
 
-enum : uint32_t { VAR_SHIFTOR = 1, VAR_QGRAM = 2, VAR_LINEAR = 3 };
+enum : uint32_t { VAR_SHIFTOR = 1, VAR_QGRAM = 2, VAR_LINEAR = 3, VAR_DFA = 4 };
+
+// Largest automaton (transition table bytes) a DFA plan may have: the table
+// lives in shared memory beside the kernel's other buffers.
+constexpr uint32_t DFA_MAX_TABLE = 32768 - 256;
 
 // Device header of a plan blob.  The blob is one contiguous, 256-byte
 // aligned allocation: header, then the tables at the listed byte offsets.
@@ -29,10 +33,21 @@ struct PlanDev {
     uint32_t off_slots;   // QSlot[1 << slot_bits]
     uint32_t off_offs;    // u16 offsets j of each q-gram, descending per key
     uint32_t off_fail;    // u32 border table fail[0..m] (Knuth-Morris-Pratt)
-    uint32_t tile_starts; // start positions per work item (QGRAM / LINEAR)
+    uint32_t tile_starts; // start positions per work item (QGRAM / LINEAR / DFA)
     uint32_t bytes;       // blob size
+    // String-matching automaton over a class-reduced alphabet (DFA plans,
+    // and q-gram plans of periodic patterns for their dense fallback; 0 =
+    // none).  Rows are addressed by byte offset r = 2 * C * state and
+    // cls[c] = 2 * class of byte c (class 0: bytes absent from p); the u16 at
+    // byte offset r + cls[c] of the table is the row offset of the next
+    // state, so a step is two loads and one add.
+    uint32_t off_cls;     // 256 x u8
+    uint32_t off_dfa;     // (m + 1) x C x u16
+    uint32_t classes;     // C
+    uint32_t dfa_final;   // row offset of state m (a match ends here)
+    uint32_t reserved[12];
 };
-static_assert(sizeof(PlanDev) == 64, "PlanDev is one 64-byte header");
+static_assert(sizeof(PlanDev) == 128, "PlanDev is one 128-byte header");
 
 struct QSlot {
     uint64_t key;    // q-gram packed little-endian (byte 0 in bits 0..7)

@@ -23,7 +23,8 @@ enum KernelId : int {
     K_QGRAM = 6,  // exact q-gram stride filter + warp verification
     K_LINEAR = 7, // per-segment Knuth-Morris-Pratt
     K_SOMULTI = 8, // several Shift-And patterns (m <= 16) of one text in one state (batches only)
-    K_COUNT = 9
+    K_DFA = 9,     // per-segment string-matching automaton, table in shared memory
+    K_COUNT = 10
 };
 
 inline bool so_kid(int kid) { return kid <= K_SO64A; }

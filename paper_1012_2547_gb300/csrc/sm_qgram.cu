@@ -1,6 +1,7 @@
 // Long patterns: exact q-gram stride filter with warp-cooperative
-// verification, and the per-segment Knuth-Morris-Pratt scan that serves as
-// its linear-time fallback (and as a kernel family of its own).
+// verification, and two linear-time per-segment scans that serve as its
+// fallback and as kernel families of their own: Knuth-Morris-Pratt, and the
+// string-matching automaton (the AUT/DFA algorithm of the paper's tables).
 //
 // Filter (the Hash-q idea of Fig. 1, with q-grams compared exactly).  Let
 // s = m - q + 1.  Any occurrence [i, i+m-1] contains exactly one position
@@ -18,8 +19,19 @@
 //
 // Density guard: a warp that spends more than a fixed number of verification
 // rounds per probe (periodic patterns on periodic text, e.g. a^m in a^n)
-// flags the tile, which is then recomputed with the linear scan: per thread,
-// Knuth-Morris-Pratt over its start range plus m-1 bytes, O(range + m).
+// flags the tile, which is then recomputed with a linear scan per thread
+// over its start range plus m-1 bytes, O(range + m): the automaton (read
+// through the L1 cache) when the plan carries one -- periodic patterns, the
+// only ones that can occur densely -- else Knuth-Morris-Pratt.
+//
+// Automaton.  delta(q, c) is the length of the longest prefix of p that is a
+// suffix of p[0..q-1] c (q = m after a match); the automaton started in
+// state 0 at L reaches state m exactly at the ends of the occurrences that
+// start at or after L.  Bytes absent from p share one class, whose
+// transitions all go to state 0, so the table has (m+1) x C entries for C-1
+// distinct pattern bytes.  The DFA kernel keeps it in shared memory; a step
+// is two shared loads (class, then transition) and one add, the same for
+// every m.
 //
 // Compaction is the same as in the bit-parallel kernel: per-thread counts,
 // block scan, decoupled look-back, ordered writes.  Per-thread hits are
@@ -34,6 +46,9 @@ namespace {
 constexpr int QG_THREADS = 128;
 constexpr int QG_HB = 8;              // buffered hits per thread
 constexpr int QG_ROUNDS_PER_PROBE = 4; // density guard budget (warp rounds per probe)
+
+// Kernel families built from this file.
+enum : int { QG_QGRAM = 0, QG_KMP = 1, QG_DFA = 2 };
 
 struct QGCtl {
     unsigned long long ticket;
@@ -67,6 +82,7 @@ struct PlanView {
     const uint32_t *offs;
     const uint32_t *fail;
     uint32_t m, q, s, bm_bits, slot_bits;
+    uint32_t off_dfa;  // 0: the plan carries no automaton
 };
 
 __device__ __forceinline__ PlanView plan_view(const PlanDev *P) {
@@ -82,7 +98,25 @@ __device__ __forceinline__ PlanView plan_view(const PlanDev *P) {
     v.slots = reinterpret_cast<const QSlot *>(b + __ldg(&P->off_slots));
     v.offs = reinterpret_cast<const uint32_t *>(b + __ldg(&P->off_offs));
     v.fail = reinterpret_cast<const uint32_t *>(b + __ldg(&P->off_fail));
+    v.off_dfa = __ldg(&P->off_dfa);
     return v;
+}
+
+// An automaton: class table (2 x class per byte), transitions (row offsets),
+// and the row offset of state m.
+struct DfaView {
+    const uint16_t *cls;
+    const uint8_t *tab;
+    uint32_t fin;
+    uint32_t m;
+};
+
+// Next row offset from row offset r on byte c; SH: tables in shared memory,
+// else read-only global loads.
+template <bool SH>
+__device__ __forceinline__ uint32_t dfa_step(const DfaView &d, uint32_t r, uint32_t c) {
+    if (SH) return *reinterpret_cast<const uint16_t *>(d.tab + r + d.cls[c]);
+    return __ldg(reinterpret_cast<const uint16_t *>(d.tab + r + __ldg(d.cls + c)));
 }
 
 // Looks up q-gram g; returns the number of offsets and their first index.
@@ -208,11 +242,62 @@ __device__ void linear_range(const PlanView &v, const uint8_t *text, uint64_t n,
     }
 }
 
-template <bool QGRAM>
+// The automaton from state 0 at L: occurrences starting in
+// [L, min(L+R, n-m+1)).  Bytes are read 16 at a time where aligned.
+template <bool SH>
+__device__ __forceinline__ void dfa_range(const DfaView &d, const uint8_t *text, uint64_t n, uint64_t L,
+                                          uint64_t R, Sink &sink) {
+    const uint64_t hi = min(L + R, n - d.m + 1);
+    if (L >= hi) return;
+    const uint64_t end = hi + d.m - 1;  // bytes [L, end)
+    const uint64_t back = d.m - 1;      // end -> start
+    const uint32_t fin = d.fin;
+    uint32_t r = 0;
+    uint64_t i = L;
+    const uint64_t head = min(end, i + ((16u - (reinterpret_cast<uintptr_t>(text + i) & 15u)) & 15u));
+    for (; i < head; ++i) {
+        r = dfa_step<SH>(d, r, __ldg(text + i));
+        if (r == fin) sink.put(i - back, L);
+    }
+    for (; i + 16 <= end; i += 16) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(text + i));
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            r = dfa_step<SH>(d, r, (w[k >> 2] >> (8 * (k & 3))) & 0xffu);
+            if (r == fin) sink.put(i + k - back, L);
+        }
+    }
+    for (; i < end; ++i) {
+        r = dfa_step<SH>(d, r, __ldg(text + i));
+        if (r == fin) sink.put(i - back, L);
+    }
+}
+
+// Dense fallback of the q-gram kernel through the plan's automaton in
+// global memory (kept out of line: it must not cost the filter registers).
+__device__ __noinline__ void dfa_range_global(const PlanDev *P, const PlanView &v, const uint8_t *text,
+                                              uint64_t n, uint64_t L, uint64_t R, Sink &sink) {
+    const uint8_t *b = reinterpret_cast<const uint8_t *>(P);
+    const DfaView d{reinterpret_cast<const uint16_t *>(b + __ldg(&P->off_cls)), b + v.off_dfa,
+                    __ldg(&P->dfa_final), v.m};
+    dfa_range<false>(d, text, n, L, R, sink);
+}
+
+// Shared memory of the DFA kernel: class table and transitions.
+struct DfaShared {
+    uint16_t cls[256];
+    uint8_t tab[DFA_MAX_TABLE];
+};
+
+template <int MODE>
 __global__ void __launch_bounds__(QG_THREADS) qg_kernel(const LaunchArgs a) {
     constexpr int NW = QG_THREADS / 32;
     __shared__ QGCtl ctl;
     __shared__ uint32_t hbuf[QG_HB * QG_THREADS];
+    __shared__ __align__(16) uint8_t dfa_raw[MODE == QG_DFA ? sizeof(DfaShared) : 16];
+    DfaShared &dsm = *reinterpret_cast<DfaShared *>(dfa_raw);
+    const PlanDev *loaded = nullptr;  // plan whose automaton is in shared memory
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int warp = tid >> 5;
@@ -228,7 +313,7 @@ __global__ void __launch_bounds__(QG_THREADS) qg_kernel(const LaunchArgs a) {
                 ctl.qi = qi;
                 ctl.tile = k;
             }
-            ctl.dense = QGRAM ? 0u : 1u;
+            ctl.dense = MODE == QG_QGRAM ? 0u : 1u;
         }
         __syncthreads();
         if (ctl.ticket >= a.total) break;
@@ -240,10 +325,32 @@ __global__ void __launch_bounds__(QG_THREADS) qg_kernel(const LaunchArgs a) {
         const uint64_t L = k * R * QG_THREADS + static_cast<uint64_t>(tid) * R;
         const uint8_t *text = Q.text;
         const uint64_t n = Q.n;
+        if (MODE == QG_DFA && Q.plan != loaded) {
+            // Every thread is past its last use of the previous automaton
+            // (barrier at the end of the previous item).  Blob offsets and
+            // sizes are multiples of 16 within the 256-byte-aligned blob.
+            const uint8_t *b = reinterpret_cast<const uint8_t *>(Q.plan);
+            const uint4 *src = reinterpret_cast<const uint4 *>(b + __ldg(&Q.plan->off_cls));
+            uint4 *dst = reinterpret_cast<uint4 *>(dsm.cls);
+            for (int i = tid; i < 512 / 16; i += QG_THREADS) dst[i] = __ldg(src + i);
+            const uint32_t tbytes = (v.m + 1) * __ldg(&Q.plan->classes) * 2u;
+            src = reinterpret_cast<const uint4 *>(b + v.off_dfa);
+            dst = reinterpret_cast<uint4 *>(dsm.tab);
+            for (uint32_t i = tid; i < (tbytes + 15u) / 16u; i += QG_THREADS) dst[i] = __ldg(src + i);
+            loaded = Q.plan;
+            __syncthreads();
+        }
+        const DfaView dv{dsm.cls, dsm.tab, MODE == QG_DFA ? __ldg(&Q.plan->dfa_final) : 0u, v.m};
+        // One linear-time scan of this thread's range (count or write mode).
+        auto linear = [&](Sink &sk) {
+            if (MODE == QG_DFA) dfa_range<true>(dv, text, n, L, R, sk);
+            else if (MODE == QG_QGRAM && v.off_dfa) dfa_range_global(Q.plan, v, text, n, L, R, sk);
+            else linear_range(v, text, n, L, R, sk);
+        };
 
         // ---- count pass (q-gram filter, or linear scan for dense tiles)
         Sink sink{SINK_BUFFER, nullptr, 0, 0, hbuf + tid, 0};
-        if (QGRAM) {
+        if (MODE == QG_QGRAM) {
             const bool fine = qgram_range(v, text, n, L, R, sink, true);
             if (!__all_sync(0xffffffffu, fine) && lane == 0) ctl.dense = 1u;
         }
@@ -251,7 +358,7 @@ __global__ void __launch_bounds__(QG_THREADS) qg_kernel(const LaunchArgs a) {
         const bool dense = ctl.dense != 0;
         if (dense) {
             sink.cnt = 0;
-            linear_range(v, text, n, L, R, sink);
+            linear(sink);
         }
         const uint32_t cnt = sink.cnt;
 
@@ -298,7 +405,7 @@ __global__ void __launch_bounds__(QG_THREADS) qg_kernel(const LaunchArgs a) {
             // mode; the whole warp joins when the q-gram path needs it.
             Sink w{over ? SINK_WRITE : SINK_DISCARD, Q.out_pos, Q.cap, base, nullptr, 0};
             if (dense) {
-                if (over) linear_range(v, text, n, L, R, w);
+                if (over) linear(w);
             } else if (__any_sync(0xffffffffu, over)) {
                 qgram_range(v, text, n, L, R, w, false);
             }
@@ -310,8 +417,9 @@ __global__ void __launch_bounds__(QG_THREADS) qg_kernel(const LaunchArgs a) {
 }  // namespace
 
 const void *qg_kernel_fn(int kid) {
-    if (kid == K_QGRAM) return reinterpret_cast<const void *>(&qg_kernel<true>);
-    if (kid == K_LINEAR) return reinterpret_cast<const void *>(&qg_kernel<false>);
+    if (kid == K_QGRAM) return reinterpret_cast<const void *>(&qg_kernel<QG_QGRAM>);
+    if (kid == K_LINEAR) return reinterpret_cast<const void *>(&qg_kernel<QG_KMP>);
+    if (kid == K_DFA) return reinterpret_cast<const void *>(&qg_kernel<QG_DFA>);
     return nullptr;
 }
 

@@ -36,9 +36,20 @@ def gpu_search(text_dev, pattern: bytes, variant="auto", q=0, word_bits=0, tile=
     return out[: min(cap, total)].cpu().numpy().astype(np.uint64), total, plan
 
 
-def variants_for(m: int):
-    """(variant, q, word_bits) configurations able to serve length m."""
+DFA_MAX_TABLE = 32768 - 256  # the library's bound on an automaton's table (bytes)
+
+
+def dfa_fits(p: bytes) -> bool:
+    """The automaton of p has (m+1) x C two-byte entries, C = distinct bytes + 1."""
+    return (len(p) + 1) * (len(set(p)) + 1) * 2 <= DFA_MAX_TABLE
+
+
+def variants_for(m: int, p: bytes | None = None):
+    """(variant, q, word_bits) configurations able to serve length m (and the
+    automaton when pattern p is given and its table fits)."""
     out = [("auto", 0, 0), ("linear", 0, 0)]
+    if p is not None and dfa_fits(p):
+        out.append(("dfa", 0, 0))
     if m <= 32:
         out.append(("shiftor", 0, 32))
     if m <= 64:

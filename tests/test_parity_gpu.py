@@ -21,7 +21,7 @@ def test_single_search_1mib_sigma4_m8():
     p = gen.substring_patterns(t, 8, 1, seed=2)[0]
     exp = oracle.naive(t, p)
     dev = to_dev(t)
-    for variant, q, wb in variants_for(8):
+    for variant, q, wb in variants_for(8, p):
         got, total, _ = gpu_search(dev, p, variant, q, wb)
         assert total == len(exp), (variant, q, wb)
         assert np.array_equal(got, exp), (variant, q, wb)
@@ -39,7 +39,7 @@ def test_random_texts_all_variants(m):
             dev = to_dev(t, off)
             for p in pats:
                 exp = expect(t, p)
-                for variant, q, wb in variants_for(m):
+                for variant, q, wb in variants_for(m, p):
                     got, total, _ = gpu_search(dev, p, variant, q, wb)
                     assert total == len(exp), (sigma, n, off, variant, q, wb)
                     assert np.array_equal(got, exp), (sigma, n, off, variant, q, wb)
@@ -52,7 +52,7 @@ def test_dense_a_power(m):
         t = np.zeros(n, dtype=np.uint8)
         dev = to_dev(t, 3)
         p = bytes(m)
-        for variant, q, wb in variants_for(m):
+        for variant, q, wb in variants_for(m, p):
             got, total, _ = gpu_search(dev, p, variant, q, wb)
             assert total == n - m + 1, (n, variant, q, wb)
             assert np.array_equal(got, np.arange(n - m + 1, dtype=np.uint64)), (n, variant)
@@ -66,7 +66,7 @@ def test_periodic_patterns_on_periodic_text():
         for r in mreps:
             p = unit * r
             exp = oracle.kmp(t, p)
-            for variant, q, wb in variants_for(len(p)):
+            for variant, q, wb in variants_for(len(p), p):
                 got, total, _ = gpu_search(dev, p, variant, q, wb)
                 assert total == len(exp) and np.array_equal(got, exp), (unit, r, variant, q)
 
@@ -80,7 +80,7 @@ def test_edges_m_gt_n_empty_text_and_ends():
     assert total == 0
     for p in (b"ab", b"ij", b"abcdefghij" * 3, b"j", b"a"):
         exp = oracle.naive(t, p)
-        for variant, q, wb in variants_for(len(p)):
+        for variant, q, wb in variants_for(len(p), p):
             got, total, _ = gpu_search(dev, p, variant, q, wb)
             assert np.array_equal(got, exp), (p, variant, q, wb)
 
@@ -105,7 +105,7 @@ def test_every_offset_and_tile_boundary():
         assert np.array_equal(oracle.naive(t, p), exp)
         for off in range(16):
             dev = to_dev(t, off)
-            for variant, q, wb in variants_for(m):
+            for variant, q, wb in variants_for(m, p):
                 got, total, _ = gpu_search(dev, p, variant, q, wb)
                 assert np.array_equal(got, exp), (m, off, variant, q, wb)
 
@@ -113,7 +113,7 @@ def test_every_offset_and_tile_boundary():
 def test_truncation_reports_true_count():
     t = np.zeros(100_000, dtype=np.uint8)
     dev = to_dev(t)
-    for variant, q, wb in variants_for(4):
+    for variant, q, wb in variants_for(4, bytes(4)):
         got, total, _ = gpu_search(dev, bytes(4), variant, q, wb, cap=1000)
         assert total == 100_000 - 3
         assert np.array_equal(got, np.arange(1000, dtype=np.uint64))
@@ -132,7 +132,7 @@ def test_exhaustive_binary_pairs_n_le_12():
         for m in range(1, n + 1):
             exp = oracle.binary_masks(n, m)  # [text, pattern] -> hit bitmask
             pats = [bytes(((pv >> np.arange(m)) & 1).astype(np.uint8)) for pv in range(1 << m)]
-            for variant, q, wb in variants_for(m):
+            for variant, q, wb in variants_for(m, pats[-1]):
                 plans = smg.prepare_many(pats, variant=variant, q=q, word_bits=wb)
                 cap = (1 << n) * (n - m + 1)
                 outs = tt.full((len(pats), cap), -1, dtype=tt.int64, device="cuda")

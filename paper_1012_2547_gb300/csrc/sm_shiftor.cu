@@ -481,25 +481,75 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
             }
             const uint8_t *spill = spill_base + (hb ^ 1) * SO_SPILL_ITEM;
             const uint32_t *list = reinterpret_cast<const uint32_t *>(spill);
-            for (uint32_t r = lane; r < pend.listed; r += 32) {
-                const uint64_t idx = excl + pend.buffered + r;
-                if (idx < cap) out[idx] = static_cast<uint64_t>(ivstart + list[r] - shift);
+            // Eight loads per lane before their stores: the compiler cannot
+            // move a load of the list above a store to the output, so a
+            // load-store loop would pay one L2 round trip per 32 hits.
+            const uint64_t lbase = excl + pend.buffered;
+            for (uint32_t r0 = 0; r0 < pend.listed; r0 += 32 * 8) {
+                uint32_t v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const uint32_t r = r0 + 32u * u + lane;
+                    v[u] = r < pend.listed ? list[r] : 0u;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const uint32_t r = r0 + 32u * u + lane;
+                    if (r < pend.listed && lbase + r < cap) out[lbase + r] = static_cast<uint64_t>(ivstart + v[u] - shift);
+                }
             }
             const uint8_t *flags = spill + SO_SPILL_POS * 4;
             uint64_t run = excl + pend.buffered + pend.listed;
+            // Flag-word sub-tiles (dense ones, or past a full list) go out
+            // through the ring slot that no prefetch uses: the lanes write
+            // their hits there as 16-bit sub-tile positions at their
+            // exclusive offsets, and the warp copies them out with
+            // consecutive lanes on consecutive output words, so a warp store
+            // moves 256 contiguous bytes instead of 32 scattered words.  A
+            // sub-tile with more hits than the slot holds as 16-bit words
+            // (2,336) goes in two passes of 16 lanes (at most 2,304 hits
+            // each).
+            uint16_t *stage = reinterpret_cast<uint16_t *>(smem + (cur == 0 ? SO_NBUF - 1 : cur - 1) * SO_BUF);
+            const uint32_t half = static_cast<uint32_t>(lane) >> 4;
+            // The next sub-tile's flags are loaded before this one's stores
+            // (software pipelining over the L2 latency).
+            uint32_t Fn[SO_SEGC];
+            const uint16_t *fsrc = reinterpret_cast<const uint16_t *>(flags) + lane;
+#pragma unroll
+            for (int c = 0; c < SO_SEGC; ++c) Fn[c] = pend.flag_from < pend.se ? fsrc[c * 32] : 0u;
             for (uint64_t s = pend.flag_from; s < pend.se && run < cap; ++s) {
-                const uint16_t *src =
-                    reinterpret_cast<const uint16_t *>(flags + (s - pend.flag_from) * SO_SUB_FLAGS);
                 uint32_t F[SO_SEGC];
                 uint32_t cnt = 0;
+                const bool more = s + 1 < pend.se;
+                fsrc += SO_SUB_FLAGS / 2;
 #pragma unroll
                 for (int c = 0; c < SO_SEGC; ++c) {
-                    F[c] = src[c * 32 + lane];
+                    F[c] = Fn[c];
                     cnt += __popc(F[c]);
+                    Fn[c] = more ? fsrc[c * 32] : 0u;
                 }
                 uint32_t total;
                 const uint32_t ex = warp_excl_scan(cnt, &total);
-                so_write_flags(F, ex, run, cap, out, static_cast<int64_t>(s) * SO_T - shift);
+                const bool split = total > SO_BUF / 2;
+                // First hit of pass 1: lanes 16..31 when split, else none.
+                const uint32_t lo1 = split ? __shfl_sync(0xffffffffu, ex, 16) : total;
+                const int64_t base = static_cast<int64_t>(s) * SO_T - shift;
+#pragma unroll
+                for (uint32_t h = 0; h < 2; ++h) {
+                    if (h == 1 && !split) break;
+                    const uint32_t lo = h ? lo1 : 0u;
+                    const uint32_t cnt_h = h ? total - lo1 : lo1;
+                    if (!split || half == h) {
+                        uint16_t *d = stage + (ex - lo);
+                        const uint32_t r0 = static_cast<uint32_t>(lane) * SO_S;
+                        so_emit(F, [&](uint32_t b) { *d++ = static_cast<uint16_t>(r0 + b); });
+                    }
+                    __syncwarp();
+                    const uint64_t at = run + lo;
+                    const uint32_t nw = at >= cap ? 0u : cap - at < cnt_h ? static_cast<uint32_t>(cap - at) : cnt_h;
+                    for (uint32_t i = lane; i < nw; i += 32) out[at + i] = static_cast<uint64_t>(base + stage[i]);
+                    __syncwarp();
+                }
                 run += total;
             }
             return;
@@ -894,10 +944,19 @@ __global__ void __launch_bounds__(32) mp_kernel(const __grid_constant__ LaunchAr
         if (!ok) return;
         if (!pend.overflow) {
             const uint32_t *list = reinterpret_cast<const uint32_t *>(spill_base + (hb ^ 1) * SO_SPILL_ITEM);
-            uint32_t basep = 0;  // lane p: records of pattern p written so far
+            // Records of each pattern written so far, in the ring slot that
+            // no prefetch uses; the first lane of each pattern's group
+            // advances its entry by the group's size.
+            uint32_t *wbase = reinterpret_cast<uint32_t *>(smem + (cur == 0 ? SO_NBUF - 1 : cur - 1) * SO_BUF);
+            if (lane < MP_MAXK) wbase[lane] = 0;
+            __syncwarp();
+            // The next 32 records are loaded before this chunk's stores (the
+            // compiler cannot move a list load above an output store).
+            uint32_t e_next = static_cast<uint32_t>(lane) < pend.listed ? list[lane] : 0u;
             for (uint32_t c0 = 0; c0 < pend.listed; c0 += 32) {
                 const bool valid = c0 + lane < pend.listed;
-                const uint32_t e = valid ? list[c0 + lane] : 0u;
+                const uint32_t e = e_next;
+                e_next = c0 + 32 + lane < pend.listed ? list[c0 + 32 + lane] : 0u;
                 const int p = valid ? static_cast<int>(e >> 19) : 31;
                 const uint32_t rel = e & 0x7FFFFu;
                 const unsigned peers = __match_any_sync(0xffffffffu, p);
@@ -907,13 +966,12 @@ __global__ void __launch_bounds__(32) mp_kernel(const __grid_constant__ LaunchAr
                 uint64_t *op = reinterpret_cast<uint64_t *>(
                     __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(outp), p));
                 const int64_t sh = __shfl_sync(0xffffffffu, shiftp, p);
-                const uint32_t bp = __shfl_sync(0xffffffffu, basep, p);
+                const uint32_t bp = wbase[p & (MP_MAXK - 1)];
+                __syncwarp();
+                if (valid && rank == 0) wbase[p] = bp + __popc(peers);
+                __syncwarp();
                 const uint64_t idx = ex + bp + rank;
                 if (valid && idx < cp) op[idx] = static_cast<uint64_t>(ivstart + rel - sh);
-                for (uint32_t q = 0; q < kk; ++q) {
-                    const unsigned mq = __ballot_sync(0xffffffffu, valid && p == static_cast<int>(q));
-                    if (lane == static_cast<int>(q)) basep += __popc(mq);
-                }
             }
             return;
         }

@@ -325,9 +325,11 @@ sm_status build_blob(const uint8_t *p, uint32_t m, uint32_t sigma, const sm_conf
         kid = K_LINEAR;
     } else if (variant == SM_VARIANT_DFA) {
         if (!dfa_fits) return SM_EINVAL;
-        // Each thread runs the automaton over m - 1 bytes before its first
-        // start: ranges of at least 4m keep that overhead under a quarter.
-        R = std::max<uint64_t>(1024, 4ull * m);
+        // Each thread runs the automaton over m - 1 bytes past its last
+        // start.  Base ranges of max(1024, m) starts keep enough threads for
+        // texts of a few MiB; a launch over a long text gives each thread
+        // several base ranges (sub_per_item), which dilutes the overlap.
+        R = std::max<uint64_t>(1024, m);
         if (src->tile) R = std::max<uint64_t>(R, 1ull << std::min(src->tile, 24u));
         R = (R + 15) & ~uint64_t(15);
         if (R * qg_kernel_threads() >= (1ull << 32)) return SM_EINVAL;

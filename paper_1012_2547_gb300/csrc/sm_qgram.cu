@@ -173,6 +173,61 @@ struct Sink {
     }
 };
 
+// Write-mode sink of the automaton scans: a thread's hits are consecutive
+// output words, so they are gathered four at a time and written with one
+// 32-byte store once the output address is 32-byte aligned (one memory
+// request per four hits instead of one per hit on dense inputs).
+struct VSink {
+    uint64_t *out;
+    uint64_t cap;
+    uint64_t idx;
+    uint64_t b0, b1, b2, b3;  // b[4 - nb .. 3] hold the pending hits
+    uint32_t nb;
+
+    __device__ __forceinline__ void put(uint64_t i, uint64_t) {
+        if (nb == 0 && (reinterpret_cast<uintptr_t>(out + idx) & 31u)) {
+            if (idx < cap) out[idx] = i;
+            ++idx;
+            return;
+        }
+        b0 = b1;
+        b1 = b2;
+        b2 = b3;
+        b3 = i;
+        if (++nb == 4) {
+            if (idx + 4 <= cap) {
+                // No memory clobber: nothing in the kernel reads the output,
+                // and a clobber would pin the next bytes' table loads behind
+                // the store.
+                asm volatile("st.global.v4.b64 [%0], {%1, %2, %3, %4};" ::"l"(out + idx), "l"(b0), "l"(b1),
+                             "l"(b2), "l"(b3));
+            } else {  // the capacity ends inside these four words
+                if (idx < cap) out[idx] = b0;
+                if (idx + 1 < cap) out[idx + 1] = b1;
+                if (idx + 2 < cap) out[idx + 2] = b2;
+            }
+            idx += 4;
+            nb = 0;
+        }
+    }
+    // Writes the hits still pending (idx is the index of the first of them).
+    __device__ __forceinline__ void finish() {
+        if (nb >= 3) {
+            if (idx < cap) out[idx] = b1;
+            ++idx;
+        }
+        if (nb >= 2) {
+            if (idx < cap) out[idx] = b2;
+            ++idx;
+        }
+        if (nb >= 1) {
+            if (idx < cap) out[idx] = b3;
+            ++idx;
+        }
+        nb = 0;
+    }
+};
+
 // q-gram filter over start range [L, min(L+R, n-m+1)).  All lanes of the
 // warp must call it with the same R (trip counts agree).  Returns false if
 // the warp exceeded the verification budget (count mode only).
@@ -244,9 +299,9 @@ __device__ void linear_range(const PlanView &v, const uint8_t *text, uint64_t n,
 
 // The automaton from state 0 at L: occurrences starting in
 // [L, min(L+R, n-m+1)).  Bytes are read 16 at a time where aligned.
-template <bool SH>
+template <bool SH, typename S>
 __device__ __forceinline__ void dfa_range(const DfaView &d, const uint8_t *text, uint64_t n, uint64_t L,
-                                          uint64_t R, Sink &sink) {
+                                          uint64_t R, S &sink) {
     const uint64_t hi = min(L + R, n - d.m + 1);
     if (L >= hi) return;
     const uint64_t end = hi + d.m - 1;  // bytes [L, end)
@@ -275,8 +330,9 @@ __device__ __forceinline__ void dfa_range(const DfaView &d, const uint8_t *text,
 }
 
 // Dense fallback of the q-gram kernel through the plan's automaton in
-// global memory (kept out of line: it must not cost the filter registers).
-__device__ __noinline__ void dfa_range_global(const PlanDev *P, const PlanView &v, const uint8_t *text,
+// global memory (kept out of line, and with the plain sink: a function
+// called from the kernel sets the kernel's register count too).
+__device__ __forceinline__ void dfa_range_global(const PlanDev *P, const PlanView &v, const uint8_t *text,
                                               uint64_t n, uint64_t L, uint64_t R, Sink &sink) {
     const uint8_t *b = reinterpret_cast<const uint8_t *>(P);
     const DfaView d{reinterpret_cast<const uint16_t *>(b + __ldg(&P->off_cls)), b + v.off_dfa,
@@ -343,8 +399,15 @@ __global__ void __launch_bounds__(QG_THREADS) qg_kernel(const LaunchArgs a) {
         const DfaView dv{dsm.cls, dsm.tab, MODE == QG_DFA ? __ldg(&Q.plan->dfa_final) : 0u, v.m};
         // One linear-time scan of this thread's range (count or write mode).
         auto linear = [&](Sink &sk) {
-            if (MODE == QG_DFA) dfa_range<true>(dv, text, n, L, R, sk);
-            else if (MODE == QG_QGRAM && v.off_dfa) dfa_range_global(Q.plan, v, text, n, L, R, sk);
+            if (MODE == QG_DFA) {
+                if (sk.mode == SINK_WRITE) {
+                    VSink w{sk.out, sk.cap, sk.idx, 0, 0, 0, 0, 0};
+                    dfa_range<true>(dv, text, n, L, R, w);
+                    w.finish();
+                } else {
+                    dfa_range<true>(dv, text, n, L, R, sk);
+                }
+            } else if (MODE == QG_QGRAM && v.off_dfa) dfa_range_global(Q.plan, v, text, n, L, R, sk);
             else linear_range(v, text, n, L, R, sk);
         };
 

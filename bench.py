@@ -543,6 +543,36 @@ def bench_bandwidth(args, world, rank, local):
                     "GBs": round(nn / t / 1e9, 1), "variant": plans[i].info().variant,
                     "kind": "dense" if q.n else ("substring" if i % (2 * (args.per_m or 20)) < (args.per_m or 20)
                                                  else "random")})
+    # The automaton family (explicit DFA plans) beside the automatic choice:
+    # the dense stress and one substring pattern per m, where the table fits.
+    dfa = {}
+    for i, q in enumerate(queries):
+        m = len(q.pattern)
+        dense_q = bool(q.n)
+        if not dense_q and i % (2 * (args.per_m or 20)) != 0:
+            continue
+        if (m + 1) * (len(set(q.pattern)) + 1) * 2 > 32768 - 256:
+            continue
+        nn = q.n or n
+        plan = smg.prepare(q.pattern, sigma_hint=4, variant="dfa")
+        out_d = torch.empty(max(int(caps[i]), 1), dtype=torch.int64, device=dev)
+        cnt_d = torch.zeros(1, dtype=torch.int64, device=dev)
+        ts = []
+        for r in range(args.warmup + args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            smg.search_into(text, plan, out_d, cnt_d, n=nn, cap=int(caps[i]))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if r >= args.warmup:
+                ts.append(e0.elapsed_time(e1) / 1e3)
+        t = statistics.median(ts)
+        same = int(cnt_d.item()) == int(caps[i]) and bool(torch.equal(out_d[:int(caps[i])], outs[i][:int(caps[i])]))
+        key = "dense" if dense_q else "substring"
+        dfa.setdefault(str(m), {})[key] = {
+            "ms": round(t * 1e3, 4), "hits": int(caps[i]), "GBs": round(nn / t / 1e9, 1),
+            "alg_GBs": round((nn + 8 * int(caps[i])) / t / 1e9, 1), "auto_ms": res[i]["ms"],
+            "auto_variant": res[i]["variant"], "equal_to_auto": same}
     hbm, kind = peaks()
     for r in res:
         r["frac"] = round(r["GBs"] / hbm, 4)
@@ -577,7 +607,7 @@ def bench_bandwidth(args, world, rank, local):
     print(json.dumps({"workload": w.name, "metric": "scanned text GB/s (% of HBM peak) per sigma,m",
                       "peak_gbs": hbm, "peak_kind": kind, "per_m": per_m,
                       "parity_sample": {"windows": checked, "window_bytes": 1 << 20, "ok": ok},
-                      "tuning": tuning, "results": res}))
+                      "dfa": dfa, "tuning": tuning, "results": res}))
 
 
 # ---------------------------------------------------------------- batched workload

@@ -12,7 +12,9 @@ thread repeatedly
   2. admits pending requests while their device memory (own text, plan,
      output capacity, count) plus the batch workspace fits the budget,
      taking requests of one length class (floor(log2 m): the class of the
-     oldest pending request) in arrival order, up to ``max_batch``;
+     oldest pending request) in arrival order, up to ``max_batch`` requests
+     and ``max_batch_scan_bytes`` of text to scan (which bounds the GPU
+     time of a batch, and so the wait of the requests behind it);
   3. launches the batch on a free stream with ``sm_search_batch_async``
      (one persistent launch per kernel family, in memory the server owns),
      followed by the copy of the counts and an event; once the counts are
@@ -64,8 +66,9 @@ class Request:
 
 def plan_bytes_estimate(m: int) -> int:
     """Upper bound of a plan's device bytes (header, masks, pattern, q-gram
-    table, border table), for admission only."""
-    return 4096 + 64 * m
+    table, border table, and for m > 16 an automaton of at most 32 KiB),
+    for admission only."""
+    return 4096 + 64 * m + (32768 if m > 16 else 0)
 
 
 class Policy:
@@ -73,9 +76,17 @@ class Policy:
 
     def __init__(self, budget_bytes: int, max_batch: int = 512, max_wait: float = 0.0005,
                  corpus_bytes=None, workspace_per_batch: int = 128 << 20,
-                 max_batch_out_bytes: int = 1 << 62):
+                 max_batch_out_bytes: int = 1 << 62, max_batch_scan_bytes: int = 1 << 62,
+                 scan_backlog: int = 512):
         self.budget = int(budget_bytes)
         self.max_batch_out = int(max_batch_out_bytes)
+        # Text bytes one batch may scan: bounds a batch's GPU time, so a
+        # request never waits behind hundreds of long scans.  The bound
+        # grows by one step per `scan_backlog` pending requests: a backlog
+        # is drained in large batches (throughput), a short queue in small
+        # ones (latency).
+        self.max_batch_scan = int(max_batch_scan_bytes)
+        self.scan_backlog = max(1, int(scan_backlog))
         self.max_batch = int(max_batch)
         self.max_wait = float(max_wait)
         self.used = 0
@@ -86,6 +97,9 @@ class Policy:
     def need(self, r: Request) -> int:
         own = 0 if r.text is None else len(r.text)
         return own + plan_bytes_estimate(r.m) + 8 * max(r.cap, 1) + 8
+
+    def scan_bytes(self, r: Request) -> int:
+        return len(r.text) if r.text is not None else int(self.corpus_bytes.get(r.corpus, 0))
 
     def push(self, r: Request, front: bool = False) -> None:
         (self.pending.appendleft if front else self.pending.append)(r)
@@ -111,15 +125,18 @@ class Policy:
         if self.used + reserved > self.budget:
             return [], 0, rejected
         keep = collections.deque()
-        out_bytes = 0
+        out_bytes = scan = 0
+        scan_cap = self.max_batch_scan * (1 + len(self.pending) // self.scan_backlog)
         while self.pending and len(batch) < self.max_batch:
             r = self.pending.popleft()
             need = self.need(r)
             fits_out = not batch or out_bytes + 8 * r.cap <= self.max_batch_out
-            if length_class(r.m) == cls and self.used + reserved + need <= self.budget and fits_out:
+            fits_scan = not batch or scan + self.scan_bytes(r) <= scan_cap
+            if length_class(r.m) == cls and self.used + reserved + need <= self.budget and fits_out and fits_scan:
                 batch.append(r)
                 reserved += need
                 out_bytes += 8 * r.cap
+                scan += self.scan_bytes(r)
             else:
                 keep.append(r)
                 if self.used + reserved + need > self.budget and length_class(r.m) == cls:
@@ -212,7 +229,8 @@ class Server:
     def __init__(self, corpora: dict, budget_bytes: int = 40 << 30, streams: int = 4,
                  max_batch: int = 512, max_wait: float = 0.0005, first_cap: int = 256,
                  sigma_hints: dict | None = None, own_text_sigma: int = 0,
-                 staging_bytes: int = 256 << 20, pinned_pool_bytes: int | None = None):
+                 staging_bytes: int = 256 << 20, pinned_pool_bytes: int | None = None,
+                 max_batch_scan_bytes: int = 16 << 30):
         import torch
 
         import paper_1012_2547_gb300 as smg
@@ -229,7 +247,8 @@ class Server:
         self.own_text_sigma = own_text_sigma
         self.first_cap = int(first_cap)
         self.policy = Policy(budget_bytes, max_batch, max_wait,
-                             {k: v.numel() for k, v in self.corpora.items()})
+                             {k: v.numel() for k, v in self.corpora.items()},
+                             max_batch_scan_bytes=max_batch_scan_bytes)
         self.streams = [torch.cuda.Stream() for _ in range(streams)]
         self.inflight: list[dict | None] = [None] * streams
         # Per-stream pinned staging for the copy-back of small results

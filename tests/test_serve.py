@@ -63,6 +63,37 @@ def test_batch_output_cap():
     assert [r.rid for r in b3] == [3]                        # alone, though above the cap
 
 
+def test_batch_scan_cap():
+    """A batch scans at most max_batch_scan_bytes of text (corpus or own
+    text); a request alone above the cap still runs, by itself."""
+    p = Policy(budget_bytes=1 << 40, max_batch=100, workspace_per_batch=0,
+               corpus_bytes={"c": 3 << 20}, max_batch_scan_bytes=8 << 20)
+    p.push(req(0, 8))                          # corpus c: 3 MiB
+    p.push(req(1, 8, text_len=4 << 20))        # own text: 4 MiB
+    p.push(req(2, 8))                          # 3 MiB: over the cap (10 MiB)
+    p.push(req(3, 8, text_len=1 << 20))        # 1 MiB: fits (8 MiB)
+    p.push(req(4, 8, text_len=20 << 20))       # 20 MiB
+    b, _, _ = p.take()
+    assert [r.rid for r in b] == [0, 1, 3]
+    b2, _, _ = p.take()
+    assert [r.rid for r in b2] == [2]          # 3 + 20 MiB > 8 MiB
+    b3, _, _ = p.take()
+    assert [r.rid for r in b3] == [4]          # alone, though above the cap
+
+
+def test_batch_scan_cap_grows_with_backlog():
+    """With scan_backlog pending requests per step, the scan bound grows by
+    one cap per step: a backlog drains in larger batches."""
+    p = Policy(budget_bytes=1 << 40, max_batch=100, workspace_per_batch=0,
+               corpus_bytes={"c": 4 << 20}, max_batch_scan_bytes=8 << 20, scan_backlog=4)
+    for i in range(10):                        # 10 pending: bound 8 MiB x (1 + 10 // 4) = 24 MiB
+        p.push(req(i, 8))
+    b, _, _ = p.take()
+    assert [r.rid for r in b] == list(range(6))
+    b2, _, _ = p.take()                        # 4 pending: 16 MiB
+    assert [r.rid for r in b2] == [6, 7, 8, 9]
+
+
 def test_pinned_pool_size_classes():
     from paper_1012_2547_gb300.serve import PinnedPool
     for n in (1, 1 << 20, (1 << 20) + 1, 1_300_000, 3 << 20, (8 << 20) + 5, 1 << 31):

@@ -145,15 +145,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def source_hash() -> str:
-    """Hash of the CUDA sources (ties committed ncu traffic to a build)."""
+# CUDA sources the bit-parallel kernels (the dominant family) are built from.
+SHIFTAND_SOURCES = ("sm_common.cuh", "sm_internal.h", "sm_shiftor.cu")
+
+
+def source_hash(files=SHIFTAND_SOURCES) -> str:
+    """Hash of the CUDA sources a kernel is compiled from (ties committed ncu
+    traffic to the build of that kernel)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1012_2547_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(f.encode())
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(fh.read())
+    for f in sorted(files):
+        h.update(f.encode())
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 

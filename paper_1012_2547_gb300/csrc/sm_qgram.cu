@@ -314,8 +314,19 @@ __device__ __forceinline__ void dfa_range(const DfaView &d, const uint8_t *text,
         r = dfa_step<SH>(d, r, __ldg(text + i));
         if (r == fin) sink.put(i - back, L);
     }
+    // DFA kernel: the next 16 bytes are loaded before these 16 are stepped
+    // through, so the load's latency hides behind sixteen dependent table
+    // steps.  (The q-gram kernel's rare dense fallback keeps one load at a
+    // time: its registers are the filter's.)
+    uint4 nx = SH && i + 16 <= end ? __ldg(reinterpret_cast<const uint4 *>(text + i)) : make_uint4(0, 0, 0, 0);
     for (; i + 16 <= end; i += 16) {
-        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(text + i));
+        uint4 v;
+        if (SH) {
+            v = nx;
+            if (i + 32 <= end) nx = __ldg(reinterpret_cast<const uint4 *>(text + i + 16));
+        } else {
+            v = __ldg(reinterpret_cast<const uint4 *>(text + i));
+        }
         const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int k = 0; k < 16; ++k) {

@@ -157,6 +157,57 @@ sm_status sm_plan_free(sm_plan *plan);
 sm_status sm_plan_info(const sm_plan *plan, sm_plan_desc *out);
 
 /*
+ * Layout of a plan's device image (sm_plan_image).  Offsets are bytes from
+ * the start of the image; an offset of 0 means the table is absent.
+ *   masks      : 256 Shift-And masks of entry_bytes each (SHIFTOR plans),
+ *                little-endian; bit j (j < m) of mask c is 1 iff p[j] = c,
+ *                every bit >= m is 1 (Section 1's one-bit-per-symbol masks).
+ *   pattern    : the m pattern bytes.
+ *   border     : u32 fail[0..m], fail[q] = length of the longest proper
+ *                border of p[0..q-1] (Knuth-Morris-Pratt, Fig. 1).
+ *   qgram_*    : QGRAM plans.  slots: 1 << slot_bits entries of {u64 key
+ *                (q-gram, byte 0 in bits 0..7), u32 first, u32 count}
+ *                (count 0 = empty); offsets: u32, the offsets j of each key
+ *                at [first, first + count) in decreasing order; bitmap:
+ *                1 << bitmap_bits bits, bit (key * 0x9E3779B97F4A7C15) >>
+ *                (64 - bitmap_bits) set for every key.
+ *   automaton  : DFA plans, and QGRAM plans of periodic patterns (smallest
+ *                period <= m/2) whose table fits.  classes_tab: u16[256],
+ *                2 x the class of each byte (class 0: bytes absent from p);
+ *                automaton: u16[(m+1) x classes], the entry at byte offset
+ *                r + classes_tab[c] for r = 2 x classes x q is
+ *                2 x classes x delta(q, c), delta(q, c) = length of the
+ *                longest prefix of p that is a suffix of p[0..q-1] c.
+ */
+typedef struct {
+    uint32_t m;
+    uint32_t variant;      /* resolved sm_variant */
+    uint32_t kernel;       /* internal kernel id, as sm_plan_desc */
+    uint32_t bytes;        /* image size */
+    uint32_t q, s;         /* q-gram length and probe stride m - q + 1 */
+    uint32_t word_bits, hist, entry_bytes;
+    uint32_t tile_starts;  /* start positions per work unit */
+    uint32_t off_masks, off_pattern, off_border;
+    uint32_t off_qgram_bitmap, bitmap_bits, off_qgram_slots, slot_bits, off_qgram_offsets;
+    uint32_t off_classes_tab, off_automaton, classes;
+    uint32_t reserved;
+} sm_plan_layout;
+
+/*
+ * sm_plan_image - build the device image of a plan in host memory, exactly
+ * the bytes sm_prepare_ex would upload for (pattern, sigma_hint, config),
+ * without any CUDA call (plan inspection, tests, caching plans).
+ * image    : host buffer of `capacity` bytes, or NULL to ask only for the
+ *            layout (layout->bytes is the size needed).
+ * layout   : receives the layout; required.
+ * Errors: SM_EINVAL for the arguments sm_prepare_ex rejects, a null layout,
+ * or capacity < layout->bytes with a non-null image (nothing is copied).
+ */
+sm_status sm_plan_image(const uint8_t *pattern, uint32_t m, uint32_t sigma_hint,
+                        const sm_config *config, void *image, size_t capacity,
+                        sm_plan_layout *layout);
+
+/*
  * sm_search - all occurrences of pattern (host, m bytes) in text (device,
  * n bytes).  Plans are cached per pattern content, so repeated searches for
  * the same pattern skip preprocessing.

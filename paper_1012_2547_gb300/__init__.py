@@ -17,7 +17,7 @@ from . import _lib
 from ._lib import SM_ETRUNC, SmError, VARIANTS, VARIANT_NAMES, check, sm_config, sm_query
 
 __all__ = [
-    "Plan", "prepare", "prepare_many", "search", "search_into", "search_plan", "search_batch",
+    "Plan", "prepare", "prepare_many", "plan_image", "search", "search_into", "search_plan", "search_batch",
     "batch_workspace_size", "search_batch_async", "query_array", "search_batch_async_array",
     "batch_workspace_size_array",
     "Batch", "sync", "gen_text", "tuning_get", "tuning_set", "tuning_reset", "kernel_launches",
@@ -117,6 +117,25 @@ def prepare(pattern, sigma_hint: int = 0, variant="auto", q: int = 0, word_bits:
                                ctypes.byref(h))
     check(st, "sm_prepare")
     return Plan(h.value, p)
+
+
+def plan_image(pattern, sigma_hint: int = 0, variant="auto", q: int = 0, word_bits: int = 0,
+               tile: int = 0):
+    """sm_plan_image: the device image of a plan, built in host memory with
+    no CUDA call.  Returns (image as a uint8 numpy array, layout dict)."""
+    import numpy as np
+    p = _as_bytes(pattern)
+    lib = _lib.load()
+    cfg = None if variant == "auto" and not (q or word_bits or tile) else _config(variant, q, word_bits, tile)
+    cfgp = ctypes.byref(cfg) if cfg is not None else None
+    lay = _lib.sm_plan_layout()
+    check(lib.sm_plan_image(p, len(p), sigma_hint, cfgp, None, 0, ctypes.byref(lay)), "sm_plan_image")
+    img = np.zeros(lay.bytes, dtype=np.uint8)
+    check(lib.sm_plan_image(p, len(p), sigma_hint, cfgp, img.ctypes.data, img.nbytes, ctypes.byref(lay)),
+          "sm_plan_image")
+    d = {f: getattr(lay, f) for f, _ in lay._fields_}
+    d["variant"] = VARIANT_NAMES.get(d["variant"], str(d["variant"]))
+    return img, d
 
 
 def prepare_many(patterns, sigma_hint: int = 0, variant="auto", q: int = 0, word_bits: int = 0,

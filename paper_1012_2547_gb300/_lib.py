@@ -37,6 +37,13 @@ class sm_plan_desc(ctypes.Structure):
                 ("kernel", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
+class sm_plan_layout(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint32) for f in (
+        "m", "variant", "kernel", "bytes", "q", "s", "word_bits", "hist", "entry_bytes", "tile_starts",
+        "off_masks", "off_pattern", "off_border", "off_qgram_bitmap", "bitmap_bits", "off_qgram_slots",
+        "slot_bits", "off_qgram_offsets", "off_classes_tab", "off_automaton", "classes", "reserved")]
+
+
 class sm_query(ctypes.Structure):
     _fields_ = [("text", ctypes.c_void_p), ("n", ctypes.c_uint64), ("plan", ctypes.c_void_p),
                 ("out_pos", ctypes.c_void_p), ("cap", ctypes.c_uint64),
@@ -56,6 +63,8 @@ SIGNATURES = {
                               _vp, ctypes.POINTER(_vp)]),
     "sm_plan_free": (_st, [_vp]),
     "sm_plan_info": (_st, [_vp, ctypes.POINTER(sm_plan_desc)]),
+    "sm_plan_image": (_st, [_vp, _u32, _u32, ctypes.POINTER(sm_config), _vp, ctypes.c_size_t,
+                            ctypes.POINTER(sm_plan_layout)]),
     "sm_search": (_st, [_vp, _u64, _vp, _u32, _vp, _u64, _vp, _vp]),
     "sm_search_plan": (_st, [_vp, _vp, _u64, _vp, _u64, _vp, _vp]),
     "sm_search_noalloc": (_st, [_vp, _u64, _vp, _u32, _vp, _u64, _vp, _vp]),

@@ -1009,6 +1009,51 @@ sm_status sm_plan_info(const sm_plan *plan, sm_plan_desc *out) {
     return SM_OK;
 }
 
+sm_status sm_plan_image(const uint8_t *pattern, uint32_t m, uint32_t sigma_hint, const sm_config *config,
+                        void *image, size_t capacity, sm_plan_layout *layout) {
+    if (!pattern || !layout || m == 0 || m > kMaxM) return SM_EINVAL;
+    std::vector<uint8_t> blob;
+    PlanDev h{};
+    int kid = 0;
+    uint32_t min_units = 1;
+    const sm_status st = build_blob(pattern, m, sigma_hint, config, &blob, &h, &kid, &min_units);
+    if (st != SM_OK) return st;
+    sm_plan_layout d{};
+    d.m = h.m;
+    d.variant = h.variant == VAR_SHIFTOR ? SM_VARIANT_SHIFTOR
+                : h.variant == VAR_QGRAM ? SM_VARIANT_QGRAM
+                : h.variant == VAR_DFA   ? SM_VARIANT_DFA
+                                         : SM_VARIANT_LINEAR;
+    d.kernel = static_cast<uint32_t>(kid);
+    d.bytes = h.bytes;
+    d.q = h.q;
+    d.s = h.s;
+    d.word_bits = h.word_bits;
+    d.hist = h.hist;
+    d.tile_starts = static_cast<uint32_t>(kernel_tile_starts(kid, h));
+    if (h.variant == VAR_SHIFTOR) {
+        d.entry_bytes = so_entry_bytes(kid);
+        d.off_masks = h.off_tbl;
+    }
+    d.off_pattern = h.off_pat;
+    d.off_border = h.off_fail;
+    if (h.variant == VAR_QGRAM) {
+        d.off_qgram_bitmap = h.off_bitmap;
+        d.bitmap_bits = h.bm_bits;
+        d.off_qgram_slots = h.off_slots;
+        d.slot_bits = h.slot_bits;
+        d.off_qgram_offsets = h.off_offs;
+    }
+    d.off_classes_tab = h.off_cls;
+    d.off_automaton = h.off_dfa;
+    d.classes = h.classes;
+    *layout = d;
+    if (!image) return SM_OK;
+    if (capacity < blob.size()) return SM_EINVAL;
+    std::memcpy(image, blob.data(), blob.size());
+    return SM_OK;
+}
+
 sm_status sm_search_plan(const sm_plan *plan, const uint8_t *text, uint64_t n, uint64_t *out_pos,
                          uint64_t cap, uint64_t *out_count, sm_stream_t stream) {
     return search_plan_impl(plan, text, n, out_pos, cap, out_count, stream);

@@ -345,18 +345,35 @@ sm_status build_blob(const uint8_t *p, uint32_t m, uint32_t sigma, const sm_conf
     const bool with_dfa =
         h.variant == VAR_DFA || (h.variant == VAR_QGRAM && dfa_fits && 2ull * (m - fail[m]) <= m);
 
-    // q-gram table: (packed q-gram, offset) pairs sorted by q-gram, then by
-    // offset descending, so each distinct q-gram is one run of its offsets
-    // in the order the kernel emits candidates.
-    std::vector<std::pair<uint64_t, uint32_t>> grams;
+    // q-gram table, in O(m): the packed q-gram of every offset j (rolled
+    // from the previous one), and the number of distinct ones, counted in a
+    // scratch hash set, which sizes the table.
+    std::vector<uint64_t> keys;
     uint32_t nkeys = 0;
     if (h.variant == VAR_QGRAM) {
-        grams.reserve(m - q + 1);
-        for (uint32_t j = 0; j + q <= m; ++j) grams.emplace_back(pack_qgram(p + j, q), j);
-        std::sort(grams.begin(), grams.end(), [](const auto &x, const auto &y) {
-            return x.first != y.first ? x.first < y.first : x.second > y.second;
-        });
-        for (size_t i = 0; i < grams.size(); ++i) nkeys += i == 0 || grams[i].first != grams[i - 1].first;
+        const uint32_t ng = m - q + 1;
+        keys.resize(ng);
+        uint64_t g = pack_qgram(p, q);
+        const uint32_t top = 8 * (q - 1);
+        for (uint32_t j = 0; j < ng; ++j) {
+            keys[j] = g;
+            if (j + q < m) g = (g >> 8) | (static_cast<uint64_t>(p[j + q]) << top);
+        }
+        thread_local std::vector<uint64_t> seen_key;
+        thread_local std::vector<uint8_t> seen_used;
+        const uint32_t sbits = std::max(4u, ceil_log2(2ull * ng));
+        seen_key.assign(size_t(1) << sbits, 0);
+        seen_used.assign(size_t(1) << sbits, 0);
+        const uint32_t smask = (1u << sbits) - 1;
+        for (uint32_t j = 0; j < ng; ++j) {
+            uint32_t sl = static_cast<uint32_t>((keys[j] * 0x9E3779B97F4A7C15ull) >> (64 - sbits));
+            while (seen_used[sl] && seen_key[sl] != keys[j]) sl = (sl + 1) & smask;
+            if (!seen_used[sl]) {
+                seen_used[sl] = 1;
+                seen_key[sl] = keys[j];
+                ++nkeys;
+            }
+        }
         h.slot_bits = std::max(4u, ceil_log2(2ull * nkeys));
         h.bm_bits = std::min(16u, std::max(10u, h.slot_bits + 4));
     }
@@ -409,20 +426,33 @@ sm_status build_blob(const uint8_t *p, uint32_t m, uint32_t sigma, const sm_conf
         QSlot *slots = reinterpret_cast<QSlot *>(b + h.off_slots);
         uint32_t *offs = reinterpret_cast<uint32_t *>(b + h.off_offs);
         const uint32_t mask = (1u << h.slot_bits) - 1;
-        for (size_t i = 0; i < grams.size();) {
-            const uint64_t g = grams[i].first;
-            size_t e = i;
-            while (e < grams.size() && grams[e].first == g) ++e;
+        const uint32_t ng = m - q + 1;
+        // Each key gets a slot (linear probing from its hash) and a count;
+        // then each slot a run of the offsets array; then the runs are
+        // filled with j descending, the order the kernel emits candidates.
+        std::vector<uint32_t> slot_of(ng);
+        for (uint32_t j = 0; j < ng; ++j) {
+            const uint64_t g = keys[j];
             const uint64_t hh = g * 0x9E3779B97F4A7C15ull;
-            const uint32_t bb = static_cast<uint32_t>(hh >> (64 - h.bm_bits));
-            bitmap[bb >> 5] |= 1u << (bb & 31);
             uint32_t sl = static_cast<uint32_t>(hh >> (64 - h.slot_bits));
-            while (slots[sl].count) sl = (sl + 1) & mask;
-            slots[sl].key = g;
-            slots[sl].first = static_cast<uint32_t>(i);
-            slots[sl].count = static_cast<uint32_t>(e - i);
-            for (size_t r = i; r < e; ++r) offs[r] = grams[r].second;  // descending j within the run
-            i = e;
+            while (slots[sl].count && slots[sl].key != g) sl = (sl + 1) & mask;
+            if (!slots[sl].count) {
+                slots[sl].key = g;
+                const uint32_t bb = static_cast<uint32_t>(hh >> (64 - h.bm_bits));
+                bitmap[bb >> 5] |= 1u << (bb & 31);
+            }
+            ++slots[sl].count;
+            slot_of[j] = sl;
+        }
+        std::vector<uint32_t> fill(mask + 1, 0);
+        uint32_t run = 0;
+        for (uint32_t sl = 0; sl <= mask; ++sl) {
+            slots[sl].first = run;
+            run += slots[sl].count;
+        }
+        for (uint32_t j = ng; j-- > 0;) {
+            const uint32_t sl = slot_of[j];
+            offs[slots[sl].first + fill[sl]++] = j;
         }
     }
     std::memcpy(b + h.off_fail, fail.data(), 4ull * (m + 1));
@@ -452,6 +482,23 @@ sm_status build_blob(const uint8_t *p, uint32_t m, uint32_t sigma, const sm_conf
     return SM_OK;
 }
 
+// Pinned host staging for plan uploads, reused across calls: a copy from
+// pageable memory goes through a driver bounce buffer at a fraction of the
+// link's rate.  Its mutex is held from the fill to the stream sync that
+// follows the copy, so the buffer is never rewritten while in flight.
+struct PinnedStaging {
+    std::mutex mu;
+    uint8_t *p = nullptr;
+    size_t cap = 0;
+};
+
+PinnedStaging &pinned_staging() {
+    static PinnedStaging *s = new PinnedStaging();  // never destroyed: may be used at exit
+    return *s;
+}
+
+constexpr size_t kStagingMax = size_t(1) << 30;  // larger uploads stage in pageable memory
+
 sm_status prepare_many(const uint8_t *patterns, const uint32_t *lengths, uint32_t count,
                        uint32_t sigma, const sm_config *cfg, cudaStream_t stream, sm_plan **out) {
     sm_status st = ensure_init();
@@ -471,20 +518,21 @@ sm_status prepare_many(const uint8_t *patterns, const uint32_t *lengths, uint32_
     std::vector<sm_status> sts(count, SM_OK);
     const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
     const unsigned nth = static_cast<unsigned>(std::min<uint64_t>(std::min(hw, 16u), (pos >> 14) + 1));
-    auto work = [&](unsigned t) {
+    auto on_threads = [&](auto &&fn) {
+        if (nth <= 1 || count < 64) {
+            for (unsigned t = 0; t < nth; ++t) fn(t);
+        } else {
+            std::vector<std::thread> pool;
+            for (unsigned t = 1; t < nth; ++t) pool.emplace_back(fn, t);
+            fn(0);
+            for (auto &th : pool) th.join();
+        }
+    };
+    on_threads([&](unsigned t) {
         for (uint32_t i = t; i < count; i += nth)
             sts[i] = build_blob(patterns + pat_off[i], lengths[i], sigma, cfg, &blobs[i], &hdrs[i], &kids[i],
                                 &min_units[i]);
-    };
-    if (nth <= 1 || count < 64) {
-        work(0);
-        for (unsigned t = 1; t < nth; ++t) work(t);
-    } else {
-        std::vector<std::thread> pool;
-        for (unsigned t = 1; t < nth; ++t) pool.emplace_back(work, t);
-        work(0);
-        for (auto &th : pool) th.join();
-    }
+    });
     size_t total = 0;
     std::vector<size_t> offs(count);
     for (uint32_t i = 0; i < count; ++i) {
@@ -492,14 +540,38 @@ sm_status prepare_many(const uint8_t *patterns, const uint32_t *lengths, uint32_
         offs[i] = total;
         total += blobs[i].size();
     }
-    std::vector<uint8_t> host(total);
-    for (uint32_t i = 0; i < count; ++i) std::memcpy(host.data() + offs[i], blobs[i].data(), blobs[i].size());
     auto arena = std::make_shared<DevArena>();
     SM_TRY_CUDA(BlockPool::get().acquire(std::max<size_t>(total, 256), &arena->ptr, &arena->cls));
+    PinnedStaging &ps = pinned_staging();
+    std::lock_guard<std::mutex> staging_lock(ps.mu);
+    uint8_t *stage = nullptr;
+    std::vector<uint8_t> pageable;
+    if (total <= kStagingMax) {
+        if (ps.cap < total) {
+            if (ps.p) cudaFreeHost(ps.p);
+            ps.p = nullptr;
+            ps.cap = 0;
+            const size_t want = std::min(kStagingMax, std::max<size_t>(total + total / 2, size_t(16) << 20));
+            if (cudaHostAlloc(reinterpret_cast<void **>(&ps.p), want, cudaHostAllocDefault) == cudaSuccess) {
+                ps.cap = want;
+            } else {
+                ps.p = nullptr;
+                (void)cudaGetLastError();  // not sticky: stage in pageable memory instead
+            }
+        }
+        if (ps.cap >= total) stage = ps.p;
+    }
+    if (!stage) {
+        pageable.resize(total);
+        stage = pageable.data();
+    }
+    on_threads([&](unsigned t) {
+        for (uint32_t i = t; i < count; i += nth) std::memcpy(stage + offs[i], blobs[i].data(), blobs[i].size());
+    });
     // Upload on the caller's stream, then wait for it: the plans are usable
     // by work on any stream once this returns, and no legacy-default-stream
     // copy serialises with other streams' work.
-    SM_TRY_CUDA(cudaMemcpyAsync(arena->ptr, host.data(), total, cudaMemcpyHostToDevice, stream));
+    SM_TRY_CUDA(cudaMemcpyAsync(arena->ptr, stage, total, cudaMemcpyHostToDevice, stream));
     SM_TRY_CUDA(cudaStreamSynchronize(stream));
     pos = 0;
     for (uint32_t i = 0; i < count; ++i) {

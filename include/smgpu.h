@@ -337,6 +337,17 @@ sm_status sm_sync(sm_stream_t stream);
  */
 uint64_t sm_kernel_launches(void);
 
+/*
+ * sm_selftest_wait - failure-reporting check.  Enqueues on `stream` one
+ * warp that resolves a look-back word whose predecessor nothing ever
+ * publishes: the library's bounded wait runs out after its limit (2 s of
+ * device time), the kernel records the timeout in the device error word
+ * and returns, and the next sm_sync(stream) reports SM_ETIMEOUT (and clears
+ * it).  The stream and context stay usable.  Returns SM_ECUDA if the launch
+ * fails.
+ */
+sm_status sm_selftest_wait(sm_stream_t stream);
+
 /* Release library-owned workspace and cached plans.  No work may be pending. */
 sm_status sm_shutdown(void);
 

@@ -63,6 +63,7 @@ SIGNATURES = {
                               _vp, ctypes.POINTER(_vp)]),
     "sm_plan_free": (_st, [_vp]),
     "sm_plan_info": (_st, [_vp, ctypes.POINTER(sm_plan_desc)]),
+    "sm_selftest_wait": (_st, [_vp]),
     "sm_plan_image": (_st, [_vp, _u32, _u32, ctypes.POINTER(sm_config), _vp, ctypes.c_size_t,
                             ctypes.POINTER(sm_plan_layout)]),
     "sm_search": (_st, [_vp, _u64, _vp, _u32, _vp, _u64, _vp, _vp]),

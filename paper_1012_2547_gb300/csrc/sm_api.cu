@@ -1299,6 +1299,33 @@ sm_status sm_sync(sm_stream_t stream) {
 
 uint64_t sm_kernel_launches(void) { return lib().launches.load(); }
 
+namespace smgpu {
+namespace {
+
+// One warp resolves look-back word 1 whose predecessor (word 0) stays
+// empty: the bounded wait runs out, records ERR_TIMEOUT and returns.
+__global__ void selftest_wait_kernel(uint64_t *state, uint32_t *err) {
+    bool ok = true;
+    lookback_resolve(state, 1, 0, err, &ok);
+}
+
+}  // namespace
+}  // namespace smgpu
+
+sm_status sm_selftest_wait(sm_stream_t stream) {
+    sm_status st = ensure_init();
+    if (st != SM_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint8_t *ws = nullptr;
+    st = get_workspace(s, 256, &ws);
+    if (st != SM_OK) return st;
+    uint64_t *state = reinterpret_cast<uint64_t *>(ws);
+    SM_TRY_CUDA(cudaMemsetAsync(state, 0, 2 * sizeof(uint64_t), s));
+    smgpu::selftest_wait_kernel<<<1, 32, 0, s>>>(state, lib().err);
+    SM_TRY_CUDA(cudaGetLastError());
+    return SM_OK;
+}
+
 sm_status sm_shutdown(void) {
     Lib &L = lib();
     std::lock_guard<std::mutex> g(L.mu);

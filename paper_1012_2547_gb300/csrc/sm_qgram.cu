@@ -341,8 +341,9 @@ __device__ __forceinline__ void dfa_range(const DfaView &d, const uint8_t *text,
 }
 
 // Dense fallback of the q-gram kernel through the plan's automaton in
-// global memory (kept out of line, and with the plain sink: a function
-// called from the kernel sets the kernel's register count too).
+// global memory.  Inlined, with the plain sink and one text load at a time:
+// a call frame, the vector sink or a second load in flight would each raise
+// the filter kernel's register count or add spills to its hot path.
 __device__ __forceinline__ void dfa_range_global(const PlanDev *P, const PlanView &v, const uint8_t *text,
                                               uint64_t n, uint64_t L, uint64_t R, Sink &sink) {
     const uint8_t *b = reinterpret_cast<const uint8_t *>(P);

@@ -47,6 +47,8 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 FALLBACK_HBM_GBS = 6800.0
+SM_MAX_MHZ = 2070.0
+METRIC = "scanned text GB/s (% of HBM peak) per sigma,m; served queries/s + p50/p99 latency"
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -161,20 +163,25 @@ def source_hash(files=SHIFTAND_SOURCES) -> str:
     return h.hexdigest()[:16]
 
 
-def committed_traffic(kernel: str):
-    """dram read+write bytes per launch from profiles/traffic.txt when it was
-    taken on the current sources, else None."""
+def committed_profile(kernel: str) -> dict:
+    """Per-launch ncu figures of `kernel` (dram bytes, thread instructions)
+    from profiles/traffic.txt, when they were taken on the current sources;
+    else {}."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
-        return None, None
+        return {}
     cur = source_hash()
     for line in open(path):
         if line.startswith("#") or not line.strip():
             continue
         kv = dict(x.split("=", 1) for x in line.split() if "=" in x)
         if kv.get("kernel") == kernel and kv.get("source") == cur:
-            return float(kv["bytes_per_launch"]), kv.get("units_per_launch")
-    return None, None
+            out = {}
+            for k in ("bytes_per_launch", "inst_per_launch"):
+                if k in kv:
+                    out[k] = float(kv[k])
+            return out
+    return {}
 
 
 # ---------------------------------------------------------------- CPU oracle timing
@@ -204,6 +211,27 @@ def cpu_sample_time(texts, queries, budget_s: float, threads: int):
 
 
 # ---------------------------------------------------------------- our arm
+
+def load_tuning(args, sigmas=None):
+    """Apply the committed GB300 tuning table (or, with --tune, re-measure
+    it on this device); None with --no-tune."""
+    if args.no_tune:
+        return None
+    from paper_1012_2547_gb300 import tuner
+    if args.tune or not os.path.exists(tuner.GB300_TABLE):
+        kw = {"sigmas": sigmas} if sigmas else {}
+        return {"seconds": tuner.tune(**kw)["seconds"], "source": "measured now"}
+    tr = tuner.load(tuner.GB300_TABLE)
+    return {"seconds": tr["seconds"],
+            "source": "paper_1012_2547_gb300/tuning_gb300.json (measured on GB300 by tuner.tune)"}
+
+
+def workload_config(w, world: int) -> dict:
+    """The `config` object of both arms' JSON lines."""
+    return {"workload": w.name, "searches": len(w.queries), "scanned_bytes_per_step": w.scanned_bytes,
+            "parallelism": f"replicas{world}",
+            "l2": "GPU arm: L2 flushed by a 256 MiB write before each timed step"}
+
 
 def sweep_kwargs(args) -> dict:
     """Subset of the sweep for profiling small cases (--ms, --per-m)."""
@@ -300,21 +328,30 @@ def run_ours(args, world, rank, local):
                 outbuf[int(offs[i]):int(offs[i + 1])], counts[i:i + 1]) for i in idx]
         alg = sum(len(texts_h[queries[i].text_id]) for i in idx) + 8 * int(cnt_h[idx].sum())
         batches.append({"key": key, "batch": smg.Batch(its, graph=True), "alg_bytes": alg,
+                        "scanned": sum(len(texts_h[queries[i].text_id]) for i in idx),
                         "n": len(idx), "times": []})
 
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in batches]
+    ev_step = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
 
     def step(record: bool):
+        # One event pair around the whole step (gaps between the families'
+        # graph launches included); one pair per family inside it gives the
+        # families' shares.
+        ev_step[0].record(stream)
         for b, (e0, e1) in zip(batches, ev):
             e0.record(stream)
             b["batch"].launch(stream)
             e1.record(stream)
+        ev_step[1].record(stream)
         if record:
             torch.cuda.synchronize()
             for b, (e0, e1) in zip(batches, ev):
                 b["times"].append(e0.elapsed_time(e1) / 1e3)
+            return ev_step[0].elapsed_time(ev_step[1]) / 1e3
+        return None
 
     # The steps run inside an NVTX range, so a profiler can be limited to
     # them (ncu --nvtx --nvtx-include bench_steps/) and skip the tuner's
@@ -339,8 +376,7 @@ def run_ours(args, world, rank, local):
     for _ in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize()
-        step(True)
-        step_times.append(sum(b["times"][-1] for b in batches))
+        step_times.append(step(True))
     torch.cuda.synchronize()
     launches = smg.kernel_launches() - launches0
     if nvtx is not None:
@@ -396,16 +432,39 @@ def run_ours(args, world, rank, local):
     hbm, peak_kind = peaks()
     dom = max(batches, key=lambda b: statistics.mean(b["times"]))
     dom_t = statistics.mean(dom["times"])
-    achieved = dom["alg_bytes"] / dom_t / 1e9
     kname = family_name(dom["key"])
-    traffic, _ = committed_traffic(kname + ":" + w.name)
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(achieved / hbm, 4), "traffic": traffic, "kernel": kname,
-                "peak_kind": peak_kind, "kernel_ms": round(dom_t * 1e3, 4),
-                "kernel_share": round(dom_t / per_step, 4),
-                "families": {family_name(b["key"]): {"searches": b["n"],
-                                                      "ms": round(statistics.mean(b["times"]) * 1e3, 4)}
-                             for b in batches}}
+    prof = committed_profile(kname + ":" + w.name)
+    traffic = prof.get("bytes_per_launch")
+    achieved = dom["alg_bytes"] / dom_t / 1e9
+    hbm_view = {"achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "peak_kind": peak_kind}
+    # Issue ceiling: SMs x 4 schedulers x 32 lanes x SM clock (thread
+    # instructions per second); the clock is the median sampled under load.
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = (clk or {}).get("sm_mhz") or SM_MAX_MHZ
+    issue_peak = sms * 128 * mhz * 1e6 / 1e9  # G thread instructions / s
+    issue = {"peak": round(issue_peak, 1), "unit": "Ginst/s",
+             "peak_basis": f"{sms} SMs x 128 lanes x {mhz:.0f} MHz"}
+    if "inst_per_launch" in prof:
+        ach_i = prof["inst_per_launch"] / dom_t / 1e9
+        issue.update({"achieved": round(ach_i, 1), "frac": round(ach_i / issue_peak, 4),
+                      "inst_per_scanned_byte": round(prof["inst_per_launch"] / dom["scanned"], 3),
+                      "inst_basis": "smsp__thread_inst_executed.sum per launch, committed ncu capture"})
+    # The family's texts stay in L2 across its searches when its DRAM traffic
+    # is well under its algorithmic bytes; then issue, not HBM, bounds it.
+    l2_fed = traffic is not None and traffic < 0.5 * dom["alg_bytes"]
+    if l2_fed and "achieved" in issue:
+        roofline = {"bound": "alu", "achieved": issue["achieved"], "peak": issue["peak"],
+                    "unit": "Ginst/s", "frac": issue["frac"], "traffic": traffic, "hbm_view": hbm_view}
+    else:
+        roofline = {"bound": "hbm", "achieved": hbm_view["achieved"], "peak": hbm, "unit": "GB/s",
+                    "frac": hbm_view["frac"], "traffic": traffic, "issue": issue}
+    roofline.update({
+        "kernel": kname, "peak_kind": peak_kind, "alg_bytes_per_launch": dom["alg_bytes"],
+        "kernel_ms": round(dom_t * 1e3, 4), "kernel_share": round(dom_t / per_step, 4),
+        "families": {family_name(b["key"]): {"searches": b["n"],
+                                             "ms": round(statistics.mean(b["times"]) * 1e3, 4)}
+                     for b in batches}})
 
     # e2e through the C ABI from pinned host buffers: texts H2D, plans built
     # and uploaded (sm_prepare_many), the batch described by pointer arrays
@@ -459,7 +518,7 @@ def run_ours(args, world, rank, local):
                "sample": f"{k} of {nq} sweep searches ({b / 1e9:.2f} GB), threaded naive"}
 
     return {
-        "metric": "scanned text GB/s (% of HBM peak) per sigma,m",
+        "metric": METRIC,
         "value": round(value, 2),
         "unit": "GB/s",
         "n_gpus": world,
@@ -471,10 +530,9 @@ def run_ours(args, world, rank, local):
         "vs_baseline": None,
         "dtype": "u8",
         "data": "synthetic",
-        "config": {"workload": w.name, "searches": nq, "scanned_bytes_per_step": scanned,
-                   "positions_per_step": total_hits, "l2": "flushed (256 MiB write) before each step",
-                   "parallelism": f"replicas{world}"},
-        "pct_of_hbm_peak": round(100 * value / world / hbm, 2),
+        "config": workload_config(w, world),
+        "positions_per_step": total_hits,
+        "scanned_over_copy_peak_pct": round(100 * value / world / hbm, 2),
         "roofline": roofline,
         "e2e": e2e,
         "cpu_baseline": cpu,
@@ -488,12 +546,21 @@ def run_ours(args, world, rank, local):
 
 # ---------------------------------------------------------------- bandwidth workload
 
-def bench_bandwidth(args, world, rank, local):
+def _kernel_of(plan) -> str:
+    return family_name(plan.info().kernel)
+
+
+def bandwidth_record(args, local, compact: bool = False) -> dict:
+    """Single-pattern scans of the 8 GiB sigma = 4 text (m in {4, 32, 256,
+    1024}: 20 substring and 20 random patterns each, one search at a time,
+    median of the timed repetitions), the a^m dense stress on its 64 MiB
+    a^n-dominated prefix, and one 1 GiB sigma = 4 scan with m = 8.  The text
+    is larger than L2, so no flush is needed between repetitions.  Full mode
+    adds the automaton family beside the automatic choice and sampled oracle
+    parity; compact mode (the default bench line) keeps the per-m medians."""
     import numpy as np
     import torch
 
-    import __graft_entry__
-    __graft_entry__.build()
     import paper_1012_2547_gb300 as smg
     from paper_1012_2547_gb300 import gen, workloads
 
@@ -501,17 +568,10 @@ def bench_bandwidth(args, world, rank, local):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     n = args.bw_bytes
-    ms = tuple(int(x) for x in args.ms.split(",")) if args.ms else workloads.BANDWIDTH_M
-    w = workloads.bandwidth(n=n, per_m=args.per_m or 20, ms=ms)
-    tuning = None
-    if not args.no_tune:
-        from paper_1012_2547_gb300 import tuner
-        if args.tune or not os.path.exists(tuner.GB300_TABLE):
-            tr = tuner.tune(sigmas=(4,), ms=ms)
-        else:
-            tr = tuner.load(tuner.GB300_TABLE)
-        tuning = {"seconds": tr["seconds"], "choices": {f"s{r['sigma']}m{r['m']}": r["best"] for r in tr["report"]
-                                                        if r["sigma"] == 4 and r["m"] in ms}}
+    ms = tuple(int(x) for x in args.ms.split(",")) if args.ms and not compact else workloads.BANDWIDTH_M
+    per_m = args.per_m if args.per_m and not compact else 20
+    warmup, reps = (2, 5) if compact else (args.warmup, args.steps)
+    w = workloads.bandwidth(n=n, per_m=per_m, ms=ms)
     spec = w.specs[0]
     text = torch.empty(n, dtype=torch.uint8, device=dev)
     smg.gen_text(text, 0, spec.key, 4)
@@ -530,30 +590,76 @@ def bench_bandwidth(args, world, rank, local):
     smg.sync()
     caps = cnt.cpu().numpy()
     outs = [torch.empty(max(int(c), 1), dtype=torch.int64, device=dev) for c in caps]
+
+    def time_search(t_text, plan, out, cnt1, nn, cap):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ts = []
+        for r in range(warmup + reps):
+            e0.record(stream)
+            smg.search_into(t_text, plan, out, cnt1, n=nn, cap=cap)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if r >= warmup:
+                ts.append(e0.elapsed_time(e1) / 1e3)
+        return statistics.median(ts)
+
     res = []
     for i, q in enumerate(queries):
         nn = q.n or n
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ts = []
-        for r in range(args.warmup + args.steps):
-            e0.record(stream)
-            smg.search_into(text, plans[i], outs[i], cnt[i:i + 1], n=nn, cap=int(caps[i]))
-            e1.record(stream)
-            torch.cuda.synchronize()
-            if r >= args.warmup:
-                ts.append(e0.elapsed_time(e1) / 1e3)
-        t = statistics.median(ts)
+        t = time_search(text, plans[i], outs[i], cnt[i:i + 1], nn, int(caps[i]))
         res.append({"m": len(q.pattern), "n": nn, "hits": int(caps[i]), "ms": round(t * 1e3, 4),
                     "GBs": round(nn / t / 1e9, 1), "variant": plans[i].info().variant,
-                    "kind": "dense" if q.n else ("substring" if i % (2 * (args.per_m or 20)) < (args.per_m or 20)
-                                                 else "random")})
+                    "kernel": _kernel_of(plans[i]),
+                    "kind": "dense" if q.n else ("substring" if i % (2 * per_m) < per_m else "random")})
+    hbm, kind = peaks()
+    for r in res:
+        r["frac"] = round(r["GBs"] / hbm, 4)
+    summary = {}
+    for m in ms:
+        for k in ("substring", "random"):
+            rs = [r for r in res if r["m"] == m and r["kind"] == k]
+            if rs:
+                g = statistics.median(r["GBs"] for r in rs)
+                summary.setdefault(str(m), {})[k] = {"GBs": round(g, 1), "frac": round(g / hbm, 4),
+                                                     "kernel": rs[0]["kernel"]}
+        d = [r for r in res if r["m"] == m and r["kind"] == "dense"]
+        if d:
+            summary[str(m)]["dense_64MiB"] = {"ms": d[0]["ms"], "hits": d[0]["hits"], "kernel": d[0]["kernel"]}
+    out = {"text": f"{n} bytes uniform sigma=4 (device-built), L2 not flushed (text > L2)",
+           "peak_gbs": hbm, "peak_kind": kind, "searches_per_m": f"{per_m} substring + {per_m} random",
+           "timing": f"median of {reps} CUDA-event timed searches after {warmup} warm-up", "per_m": summary}
+    del outs
+    # 1 GiB sigma = 4 scan with m = 8 (the single-scan figure): 10 substring patterns.
+    n1 = min(1 << 30, n)
+    sub = text[n - n1:]
+    pats = gen.substring_patterns_spec(spec, 8, 10, seed=23)
+    pl8 = smg.prepare_many(pats, sigma_hint=4)
+    c1 = torch.zeros(1, dtype=torch.int64, device=dev)
+    g8 = []
+    for p in pl8:
+        smg.search_into(sub, p, None, c1, cap=0)
+        smg.sync()
+        o1 = torch.empty(max(int(c1.item()), 1), dtype=torch.int64, device=dev)
+        t = time_search(sub, p, o1, c1, n1, o1.numel())
+        g8.append(n1 / t / 1e9)
+    g = statistics.median(g8)
+    out["scan1GiB_m8"] = {"GBs": round(g, 1), "frac": round(g / hbm, 4), "patterns": len(pl8),
+                          "kernel": _kernel_of(pl8[0])}
+    if compact:
+        del text
+        torch.cuda.empty_cache()
+        return out
     # The automaton family (explicit DFA plans) beside the automatic choice:
     # the dense stress and one substring pattern per m, where the table fits.
+    outs = [torch.empty(max(int(c), 1), dtype=torch.int64, device=dev) for c in caps]
+    for i, q in enumerate(queries):
+        smg.search_into(text, plans[i], outs[i], cnt[i:i + 1], n=q.n or n, cap=int(caps[i]))
+    smg.sync()
     dfa = {}
     for i, q in enumerate(queries):
         m = len(q.pattern)
         dense_q = bool(q.n)
-        if not dense_q and i % (2 * (args.per_m or 20)) != 0:
+        if not dense_q and i % (2 * per_m) != 0:
             continue
         if (m + 1) * (len(set(q.pattern)) + 1) * 2 > 32768 - 256:
             continue
@@ -561,32 +667,13 @@ def bench_bandwidth(args, world, rank, local):
         plan = smg.prepare(q.pattern, sigma_hint=4, variant="dfa")
         out_d = torch.empty(max(int(caps[i]), 1), dtype=torch.int64, device=dev)
         cnt_d = torch.zeros(1, dtype=torch.int64, device=dev)
-        ts = []
-        for r in range(args.warmup + args.steps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            smg.search_into(text, plan, out_d, cnt_d, n=nn, cap=int(caps[i]))
-            e1.record(stream)
-            torch.cuda.synchronize()
-            if r >= args.warmup:
-                ts.append(e0.elapsed_time(e1) / 1e3)
-        t = statistics.median(ts)
+        t = time_search(text, plan, out_d, cnt_d, nn, int(caps[i]))
         same = int(cnt_d.item()) == int(caps[i]) and bool(torch.equal(out_d[:int(caps[i])], outs[i][:int(caps[i])]))
         key = "dense" if dense_q else "substring"
         dfa.setdefault(str(m), {})[key] = {
             "ms": round(t * 1e3, 4), "hits": int(caps[i]), "GBs": round(nn / t / 1e9, 1),
             "alg_GBs": round((nn + 8 * int(caps[i])) / t / 1e9, 1), "auto_ms": res[i]["ms"],
             "auto_variant": res[i]["variant"], "equal_to_auto": same}
-    hbm, kind = peaks()
-    for r in res:
-        r["frac"] = round(r["GBs"] / hbm, 4)
-    per_m = {}
-    for m in ms:
-        for k in ("substring", "random"):
-            g = [r["GBs"] for r in res if r["m"] == m and r["kind"] == k]
-            if g:
-                per_m.setdefault(str(m), {})[k + "_GBs"] = round(statistics.median(g), 1)
-        per_m[str(m)]["frac"] = round(min(per_m[str(m)].values()) / hbm, 4)
     # Parity on samples: every hit the GPU reports inside a few windows of the
     # text, and the count there, against the oracle on the host's copy of the
     # window (regenerated from the seed).
@@ -603,15 +690,23 @@ def bench_bandwidth(args, world, rank, local):
             hi = lo + (1 << 20)
             win = spec.window(lo, hi - lo + m - 1)
             exp = oracle.naive(win, q.pattern).astype(np.int64) + lo
-            a = int(torch.searchsorted(got_all, torch.tensor([lo], device=dev)).item())
-            b = int(torch.searchsorted(got_all, torch.tensor([hi], device=dev)).item())
-            got = got_all[a:b].cpu().numpy()
-            ok &= bool(np.array_equal(got, exp))
+            a0 = int(torch.searchsorted(got_all, torch.tensor([lo], device=dev)).item())
+            b0 = int(torch.searchsorted(got_all, torch.tensor([hi], device=dev)).item())
+            ok &= bool(np.array_equal(got_all[a0:b0].cpu().numpy(), exp))
             checked += 1
-    print(json.dumps({"workload": w.name, "metric": "scanned text GB/s (% of HBM peak) per sigma,m",
-                      "peak_gbs": hbm, "peak_kind": kind, "per_m": per_m,
-                      "parity_sample": {"windows": checked, "window_bytes": 1 << 20, "ok": ok},
-                      "dfa": dfa, "tuning": tuning, "results": res}))
+    out.update({"workload": w.name, "metric": METRIC,
+                "parity_sample": {"windows": checked, "window_bytes": 1 << 20, "ok": ok},
+                "dfa": dfa, "results": res})
+    return out
+
+
+def bench_bandwidth(args, world, rank, local):
+    import __graft_entry__
+    __graft_entry__.build()
+    tuning = load_tuning(args, sigmas=(4,))
+    rec = bandwidth_record(args, local)
+    rec["tuning"] = tuning
+    print(json.dumps(rec))
 
 
 # ---------------------------------------------------------------- batched workload
@@ -650,14 +745,7 @@ def bench_batched(args, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    tuning = None
-    if not args.no_tune:
-        from paper_1012_2547_gb300 import tuner
-        if args.tune or not os.path.exists(tuner.GB300_TABLE):
-            tr = tuner.tune(sigmas=(4, 16, 64))
-        else:
-            tr = tuner.load(tuner.GB300_TABLE)
-        tuning = {"seconds": tr["seconds"]}
+    tuning = load_tuning(args, sigmas=(4, 16, 64))
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     rng = np.random.default_rng(3)
     parts = {}
@@ -751,7 +839,7 @@ def bench_batched(args, world, rank, local):
 
 # ---------------------------------------------------------------- serving workload
 
-def bench_serve(args, world, rank, local):
+def serve_record(args, local, loads=None) -> dict:
     """Serving (continuous batching) vs one launch per query, on two resident
     corpora (uniform sigma = 4 and Zipf English-like), m log-uniform in
     [2, 512], 70 % corpus queries and 30 % carrying their own text
@@ -761,8 +849,6 @@ def bench_serve(args, world, rank, local):
     import numpy as np
     import torch
 
-    import __graft_entry__
-    __graft_entry__.build()
     import paper_1012_2547_gb300 as smg
     from paper_1012_2547_gb300 import gen
     from paper_1012_2547_gb300.serve import Server
@@ -859,10 +945,10 @@ def bench_serve(args, world, rank, local):
         lat1.append(time.perf_counter() - ts)
     unb_dt = time.perf_counter() - t0
     same = all(r == c for r, c in zip(results, unb_counts))
-    loads = {}
-    for frac in args.serve_loads:
+    by_load = {}
+    for frac in (args.serve_loads if loads is None else loads):
         st, _ = run_server(arrival_rate=frac * sat["qps"])
-        loads[str(frac)] = {"offered_qps": round(frac * sat["qps"], 1), "qps": st["qps"],
+        by_load[str(frac)] = {"offered_qps": round(frac * sat["qps"], 1), "qps": st["qps"],
                             "p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
                             "batches": st["batches"], "host_s": st["host_s"],
                             "pinned_pool_bytes": st["pinned_pool_bytes"]}
@@ -877,39 +963,52 @@ def bench_serve(args, world, rank, local):
                       "p50_ms": round(float(np.percentile(lat1, 50)) * 1e3, 3),
                       "p99_ms": round(float(np.percentile(lat1, 99)) * 1e3, 3)},
         "speedup_qps": round(sat["qps"] / (len(reqs) / unb_dt), 2),
-        "poisson": loads, "counts_match_unbatched": same,
+        "poisson": by_load, "counts_match_unbatched": same,
     }
-    print(json.dumps(out), flush=True)
+    del corp
+    torch.cuda.empty_cache()
+    return out
+
+
+def bench_serve(args, world, rank, local):
+    import __graft_entry__
+    __graft_entry__.build()
+    print(json.dumps(serve_record(args, local)), flush=True)
 
 
 # ---------------------------------------------------------------- reference arm
 
 def run_reference(args, world, rank):
-    """The reference arm of this tier: the CPU oracle on the host cores."""
+    """The reference arm of this tier: the CPU oracle (threaded naive) on the
+    host cores.  Each step times a bounded sample of the workload's searches
+    (spread over texts and lengths); value = sample bytes / sample time, and
+    ms_per_step is the measured time of one sample."""
     from paper_1012_2547_gb300 import workloads
     w = workloads.sweep(**sweep_kwargs(args)) if args.workload == "sweep" else workloads.single()
     threads = os.cpu_count() or 1
     budget = max(1.0, args.ref_seconds / max(1, args.steps + args.warmup))
-    times = []
-    sample_bytes = 0
+    secs, nbytes, nsearch = [], [], []
     for r in range(args.warmup + args.steps):
         b, s, k = cpu_sample_time(w.texts, w.queries, budget, threads)
         if r >= args.warmup:
-            times.append(s / b)
-            sample_bytes = b
-    per_byte = statistics.mean(times)
-    value = 1.0 / per_byte / 1e9
-    scanned = w.scanned_bytes
+            secs.append(s)
+            nbytes.append(b)
+            nsearch.append(k)
+    value = sum(nbytes) / sum(secs) / 1e9
+    sample = (f"each step: the first ~{budget:.1f} s of searches of the workload, spread over its texts "
+              f"and lengths ({min(nsearch)}-{max(nsearch)} of {len(w.queries)} searches, "
+              f"{min(nbytes) / 1e9:.2f}-{max(nbytes) / 1e9:.2f} GB), threaded naive oracle")
     return {
         "impl": "reference",
-        "metric": "scanned text GB/s (% of HBM peak) per sigma,m",
+        "metric": METRIC,
         "value": round(value, 4), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(per_byte * scanned * 1e3, 1),
+        "warmup": args.warmup, "ms_per_step": round(statistics.mean(secs) * 1e3, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic",
-        "config": {"workload": w.name, "searches": len(w.queries), "scanned_bytes_per_step": scanned},
+        "config": workload_config(w, world),
+        "sample_bytes_per_step": round(statistics.mean(nbytes)),
         "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
-                         "sample": f"~{sample_bytes / 1e9:.2f} GB of the sweep per step, threaded naive"},
+                         "sample": sample},
         "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -938,6 +1037,8 @@ def main():
     ap.add_argument("--serve-budget", type=int, default=40 << 30)
     ap.add_argument("--serve-loads", type=float, nargs="*", default=[0.5, 0.8, 0.95])
     ap.add_argument("--serve-no-unbatched", action="store_true")
+    ap.add_argument("--no-side", action="store_true",
+                    help="default line without the bandwidth and serving records")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -965,6 +1066,12 @@ def main():
                 bench_batched(args, world, rank, local)
             return
         out = run_ours(args, world, rank, local)
+        if rank == 0 and args.workload == "sweep" and not args.no_side:
+            # The single-pattern bandwidth scans and the serving loop, in
+            # compact form, so one default run reports every half of the
+            # metric (each also runs alone: --workload bandwidth / serve).
+            out["bandwidth"] = bandwidth_record(args, local, compact=True)
+            out["serve"] = serve_record(args, local, loads=[0.5, 0.8])
         if rank == 0:
             print(json.dumps(out), flush=True)
     finally:

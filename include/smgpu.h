@@ -220,26 +220,33 @@ sm_status sm_search(const uint8_t *text, uint64_t n, const uint8_t *pattern, uin
 
 /*
  * sm_search_noalloc - sm_search for patterns of up to 64 bytes that makes no
- * device allocation at all.  The paper has no counterpart; it exists for
- * callers that cannot call cudaMalloc: code running while a stream is being
- * captured into a CUDA graph (allocation would break the capture), serving
- * loops that reserve all device memory up front and forbid allocation on
- * the request path, and plugins whose host framework owns every device
- * byte.  Those callers pass inputs and outputs only.
+ * device allocation at all.  The paper has no counterpart.  It is for
+ * callers that are not allowed to call cudaMalloc on their request path:
+ * serving loops that reserve all device memory when they start (an
+ * allocation later could fail or stall every stream while the allocator
+ * synchronises), and plugins running inside a host framework that owns
+ * every device byte through its own allocator.  Those callers pass inputs
+ * and outputs only.
  *   m          : 1..64 (longer patterns -> SM_EINVAL).
  *   n          : at most 65536 * 64 * 4608 - 16 bytes (about 19 GB); a longer
- *                text -> SM_EINVAL.
+ *                text -> SM_EINVAL, before any CUDA call.
  *   Other arguments as in sm_search.
- * The plan and the kernel's scratch (claim counter, one look-back word per
- * work item; 4.5 KiB + 512 KiB) sit in one statically sized device array
- * that every GPU loading the library keeps until exit.  The first call on
- * a device looks up that array's address (make it before any stream
- * capture).  All calls share the array and it keeps the last call's
- * contents; each call clears what must start at zero on `stream`.  Calls
- * whose GPU work overlaps (e.g. on two streams at once) race on the array:
- * order them on one stream.  *out_count is set to UINT64_MAX before the
- * launch and replaced by the total when the search completes, so a value
- * of UINT64_MAX once the stream is idle means a bounded device wait ran out.
+ * The plan and the kernel's scratch (claim counter, error word, one
+ * look-back word per work item; 4.25 KiB + 512 KiB) sit in one statically
+ * sized device array that every GPU loading the library keeps until the
+ * process exits.  The first call on a device looks up that array's address
+ * with cudaGetSymbolAddress; make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's
+ * contents: each call rewrites the plan with a small kernel (the pattern
+ * travels by value in its launch arguments) and clears what must start at
+ * zero, on `stream`.  Calls whose GPU work overlaps (e.g. on two streams at
+ * once) race on the array: order them on one stream.
+ * Completion: *out_count is set to UINT64_MAX before the search and holds
+ * the total once it completes.  A one-thread kernel enqueued after the
+ * search sets it back to UINT64_MAX if any bounded device wait of the
+ * search ran out (then out_pos may be incomplete), so once the stream is
+ * idle a count of UINT64_MAX means "failed, retry" and any other value is
+ * the exact total.  Each call adds 3 to sm_kernel_launches.
  */
 sm_status sm_search_noalloc(const uint8_t *text, uint64_t n, const uint8_t *pattern, uint32_t m,
                             uint64_t *out_pos, uint64_t cap, uint64_t *out_count,

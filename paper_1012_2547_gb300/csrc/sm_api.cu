@@ -695,6 +695,8 @@ uint64_t kernel_ntiles(int kid, const PlanDev &hdr, const uint8_t *text, uint64_
     return (n - hdr.m + 1 + T - 1) / T;
 }
 
+void count_launches(uint64_t k) { lib().launches.fetch_add(k, std::memory_order_relaxed); }
+
 cudaError_t kernel_launch(int kid, const LaunchArgs &a, int grid, cudaStream_t stream) {
     const KernelShape &s = g_shapes[kid];
     void *args[] = {const_cast<LaunchArgs *>(&a)};

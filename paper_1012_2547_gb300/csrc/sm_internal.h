@@ -62,6 +62,9 @@ uint64_t kernel_tile_starts(int kid, const PlanDev &hdr);
 // bit-parallel kernels, base ranges (tile_starts positions) otherwise.
 uint64_t kernel_ntiles(int kid, const PlanDev &hdr, const uint8_t *text, uint64_t n);
 
+// Adds k to the library's kernel-launch counter (sm_kernel_launches).
+void count_launches(uint64_t k);
+
 // Persistent launch of kernel `kid` over `a` with `grid` blocks.
 cudaError_t kernel_launch(int kid, const LaunchArgs &a, int grid, cudaStream_t stream);
 

@@ -1192,15 +1192,16 @@ size_t mp_kernel_smem() { return MPLayout::BYTES; }
 //
 // sm_search_noalloc runs the bit-parallel kernel above without any device
 // allocation: the plan (header + Shift-And masks) and the kernel's scratch
-// (claim counter and one look-back word per work item) live in the
-// file-scope array below, which every GPU that loads this library keeps
+// (claim counter, error word and one look-back word per work item) live in
+// the file-scope array below, which every GPU that loads this library keeps
 // until the process exits.  Host code must not use the array's name as a
 // device address; it takes the address from cudaGetSymbolAddress once per
-// device (the first call on a device does that set-up, so make that first
-// call before any stream capture).  All calls share the array and it keeps
-// the previous call's contents: the claim counter and the look-back words
-// are cleared on the stream before every launch, and calls whose GPU work
-// overlaps (e.g. on two streams at once) race on it.
+// device (the first call on a device does that set-up).  All calls share
+// the array and it keeps the previous call's contents: a small kernel
+// rewrites the plan from the pattern passed by value, and the claim counter,
+// error word and look-back words are cleared on the stream before every
+// launch.  Calls whose GPU work overlaps (e.g. on two streams at once) race
+// on the array.
 
 #include <mutex>
 
@@ -1230,6 +1231,36 @@ std::mutex g_noalloc_mu;
 NoAllocDevice g_noalloc_dev[NA_MAX_DEVICES];
 
 const void *na_kernel(int kid) { return smgpu::so_kernel_fn(kid); }
+
+// The pattern, passed to the plan kernel by value.
+struct NAPattern {
+    uint8_t b[64];
+};
+
+// Writes a Shift-And plan for pattern p (m <= 64) into `plan`: the header,
+// then 256 entries of esz bytes, little-endian, where bit j (j < m) of entry
+// c is 1 iff p[j] = c and every bit >= m is 1 (Section 1's one-bit-per-
+// symbol masks, with the high bits kept so older match flags survive).
+// One thread per byte value c; 256 threads.
+__global__ void na_plan_kernel(uint8_t *plan, const __grid_constant__ smgpu::PlanDev hdr,
+                               const __grid_constant__ NAPattern pat, uint32_t esz) {
+    const uint32_t c = threadIdx.x;
+    const uint32_t m = hdr.m;
+    uint64_t w = m >= 64 ? 0ull : ~((1ull << m) - 1ull);
+    for (uint32_t j = 0; j < m; ++j)
+        if (pat.b[j] == c) w |= 1ull << j;
+    uint8_t *e = plan + hdr.off_tbl + esz * c;
+    for (uint32_t k = 0; k < esz; ++k) e[k] = static_cast<uint8_t>(w >> (8 * k));
+    if (c < sizeof(smgpu::PlanDev) / 4)
+        reinterpret_cast<uint32_t *>(plan)[c] = reinterpret_cast<const uint32_t *>(&hdr)[c];
+}
+
+// Runs after the search on the same stream: if any wait of the search ran
+// out (nonzero error word), the count becomes UINT64_MAX whatever the last
+// work item wrote, so a partial result is never reported as complete.
+__global__ void na_finish_kernel(const uint32_t *err, uint64_t *out_count) {
+    if (*reinterpret_cast<const volatile uint32_t *>(err) != 0u) *out_count = ~0ull;
+}
 
 sm_status na_setup(NoAllocDevice **out) {
     int dev = 0;
@@ -1287,9 +1318,6 @@ extern "C" sm_status sm_search_noalloc(const uint8_t *text, uint64_t n, const ui
     const uint64_t items = (units + per - 1) / per;
     if (items > NA_MAX_ITEMS) return SM_EINVAL;  // cannot happen when n <= NA_MAX_N
 
-    // Plan blob on the stack: header, then the 256 Shift-And masks (bit j
-    // of B[c] is 1 iff p[j] = c; bits >= m set so older match flags survive).
-    alignas(16) uint8_t blob[sizeof(PlanDev) + 256 * 8];
     PlanDev h{};
     h.m = m;
     h.variant = VAR_SHIFTOR;
@@ -1299,20 +1327,15 @@ extern "C" sm_status sm_search_noalloc(const uint8_t *text, uint64_t n, const ui
     h.tile_starts = SO_T;
     const uint32_t esz = so_entry_bytes(kid);
     h.bytes = static_cast<uint32_t>(sizeof(PlanDev) + 256 * esz);
-    const uint64_t low = m >= 64 ? ~0ull : ((1ull << m) - 1);
-    for (int c = 0; c < 256; ++c) {
-        uint64_t w = ~low;
-        for (uint32_t j = 0; j < m; ++j)
-            if (pattern[j] == c) w |= 1ull << j;
-        memcpy(blob + sizeof(PlanDev) + esz * c, &w, esz);  // low esz bytes (little-endian)
-    }
-    memcpy(blob, &h, sizeof(h));
+    NAPattern pat{};
+    memcpy(pat.b, pattern, m);
 
     uint8_t *ctrl = d->scratch;
     uint8_t *plan = d->scratch + NA_CTRL;
     uint64_t *state = reinterpret_cast<uint64_t *>(d->scratch + NA_CTRL + NA_PLAN);
-    // The blob is staged from host memory before the copy call returns.
-    if (cudaMemcpyAsync(plan, blob, h.bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return SM_ECUDA;
+    uint32_t *err = reinterpret_cast<uint32_t *>(ctrl + 8);
+    na_plan_kernel<<<1, 256, 0, s>>>(plan, h, pat, esz);
+    if (cudaGetLastError() != cudaSuccess) return SM_ECUDA;
     if (cudaMemsetAsync(ctrl, 0, NA_CTRL, s) != cudaSuccess) return SM_ECUDA;
     if (cudaMemsetAsync(state, 0, items * sizeof(uint64_t), s) != cudaSuccess) return SM_ECUDA;
     // All-ones until the last work item writes the true total: a count of
@@ -1334,12 +1357,15 @@ extern "C" sm_status sm_search_noalloc(const uint8_t *text, uint64_t n, const ui
     a.one.sub_per_item = static_cast<uint32_t>(per);
     a.ticket = reinterpret_cast<unsigned long long *>(ctrl);
     a.total = items;
-    a.err = reinterpret_cast<uint32_t *>(ctrl + 8);
+    a.err = err;
     const uint64_t full = resident;
     const int grid = static_cast<int>(items < full ? items : full);
     void *args[] = {&a};
     if (cudaLaunchKernel(na_kernel(kid), dim3(grid), dim3(32), args, so_kernel_smem(kid), s) !=
         cudaSuccess)
         return SM_ECUDA;
+    na_finish_kernel<<<1, 1, 0, s>>>(err, out_count);
+    if (cudaGetLastError() != cudaSuccess) return SM_ECUDA;
+    count_launches(3);
     return SM_OK;
 }

@@ -27,6 +27,8 @@ then the symbol index goes through a 256-entry byte map (identity, or
 from __future__ import annotations
 
 import math
+import os
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -99,6 +101,13 @@ def zipf_probs(count: int = 90, s: float = 1.1) -> np.ndarray:
     return 1.0 / np.arange(1, count + 1, dtype=np.float64) ** s
 
 
+_BLOCK = 1 << 20
+
+
+def _threads() -> int:
+    return max(1, min(32, os.cpu_count() or 1))
+
+
 @dataclass(frozen=True)
 class TextSpec:
     """A seeded synthetic text.
@@ -131,10 +140,23 @@ class TextSpec:
         return np.asarray(self.byte_map[: len(self.thresholds) + 1], dtype=np.uint8)
 
     def window(self, start: int, count: int) -> np.ndarray:
-        """Bytes [start, start+count) of a counter-based text."""
+        """Bytes [start, start+count) of a counter-based text.  Long windows
+        are built in 1 MiB blocks on a pool of host threads (numpy's array
+        loops run without the interpreter lock)."""
         if not self.counter_based:
             raise ValueError("window() needs a counter-based text kind")
         count = max(0, min(count, self.n - start))
+        if count > _BLOCK:
+            out = np.empty(count, dtype=np.uint8)
+
+            def fill(off):
+                out[off:off + _BLOCK] = self._block(start + off, min(_BLOCK, count - off))
+            with ThreadPoolExecutor(_threads()) as ex:
+                list(ex.map(fill, range(0, count, _BLOCK)))
+            return out
+        return self._block(start, count)
+
+    def _block(self, start: int, count: int) -> np.ndarray:
         r = draws(self.key, start, count)
         u = (r >> np.uint64(32))
         if self.kind == "uniform":
@@ -146,11 +168,7 @@ class TextSpec:
     def host(self) -> np.ndarray:
         """The whole text as a host uint8 array."""
         if self.counter_based:
-            out = np.empty(self.n, dtype=np.uint8)
-            step = 1 << 24
-            for s in range(0, self.n, step):
-                out[s : s + step] = self.window(s, min(step, self.n - s))
-            return out
+            return self.window(0, self.n)
         if self.kind == "markov3":
             return markov3_text(self.n, self.seed)
         raise ValueError(self.kind)
@@ -205,7 +223,7 @@ def markov3_text(n: int, seed: int) -> np.ndarray:
             sym = (uk >= t0) + (uk >= t1) + (uk >= t2)
             out[s + k] = sym
             ctx = ((ctx << 2) | sym) & 63
-    return np.frombuffer(bytes(out), dtype=np.uint8)
+    return np.frombuffer(out, dtype=np.uint8)  # a writable view of the bytearray
 
 
 def sweep_texts(n: int = 4_194_304, seed: int = 11) -> list[TextSpec]:

@@ -14,7 +14,10 @@ def to_dev(arr: np.ndarray, offset: int = 0):
     allocation (offset != 0 gives a text pointer that is not 16-aligned)."""
     t = torch()
     buf = t.empty(len(arr) + offset + 64, dtype=t.uint8, device="cuda")
-    buf[offset: offset + len(arr)] = t.from_numpy(np.ascontiguousarray(arr)).cuda()
+    a = np.ascontiguousarray(arr)
+    if not a.flags.writeable:  # torch wants writable arrays
+        a = a.copy()
+    buf[offset: offset + len(arr)] = t.from_numpy(a).cuda()
     return buf[offset: offset + len(arr)]
 
 

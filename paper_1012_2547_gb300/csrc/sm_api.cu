@@ -197,11 +197,26 @@ uint32_t s_bucket(uint32_t sigma) {
     return std::max(1u, b);  // floor(log2 sigma) in 1..8
 }
 
+// Built-in q-gram length: the smallest q with sigma^q >= 2^11 m, clamped to
+// 3..8 (sigma 4 when unknown), so that a probe of a text q-gram that is not
+// one of the pattern's m - q + 1 q-grams passes the filter rarely: a warp's
+// round of 32 probes then reaches the key table in a few percent of rounds.
 uint32_t rule_q(uint32_t m, uint32_t sigma) {
     const double sg = sigma >= 2 ? static_cast<double>(sigma) : 4.0;
-    int q = static_cast<int>(std::ceil(std::log(64.0 * m) / std::log(sg)));
+    int q = static_cast<int>(std::ceil(std::log(2048.0 * m) / std::log(sg) - 1e-9));
     q = std::min(8, std::max(3, q));
     return std::min<uint32_t>(static_cast<uint32_t>(q), m);
+}
+
+// Built-in kernel family: the bit-parallel scan for short patterns, and for
+// m <= 64 on binary and ternary alphabets (where even 8-grams filter
+// poorly); the q-gram stride filter otherwise (from m = 17 its probes, one
+// per m - q + 1 bytes, cost fewer instructions per byte than the scan's
+// step per byte).
+uint32_t rule_variant(uint32_t m, uint32_t sigma) {
+    if (m <= 16) return SM_VARIANT_SHIFTOR;
+    if (m <= 64 && sigma >= 2 && sigma <= 3) return SM_VARIANT_SHIFTOR;
+    return SM_VARIANT_QGRAM;
 }
 
 size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -271,12 +286,11 @@ sm_status build_blob(const uint8_t *p, uint32_t m, uint32_t sigma, const sm_conf
     const bool dfa_fits = dfa_bytes <= DFA_MAX_TABLE;
 
     uint32_t variant = cfg && cfg->variant ? cfg->variant : tc.variant;
-    if (variant == SM_VARIANT_AUTO) variant = m <= 64 ? SM_VARIANT_SHIFTOR : SM_VARIANT_QGRAM;
+    if (variant == SM_VARIANT_AUTO) variant = rule_variant(m, sigma);
     // A tuned (not explicit) choice that cannot serve p falls back to the rule.
     const bool explicit_cfg = cfg && cfg->variant;
     if (!explicit_cfg && variant == SM_VARIANT_SHIFTOR && m > 64) variant = SM_VARIANT_QGRAM;
-    if (!explicit_cfg && variant == SM_VARIANT_DFA && !dfa_fits)
-        variant = m <= 64 ? SM_VARIANT_SHIFTOR : SM_VARIANT_QGRAM;
+    if (!explicit_cfg && variant == SM_VARIANT_DFA && !dfa_fits) variant = rule_variant(m, sigma);
     const sm_config *src = explicit_cfg ? cfg : &tc;
 
     PlanDev h{};
@@ -375,7 +389,10 @@ sm_status build_blob(const uint8_t *p, uint32_t m, uint32_t sigma, const sm_conf
             }
         }
         h.slot_bits = std::max(4u, ceil_log2(2ull * nkeys));
-        h.bm_bits = std::min(16u, std::max(10u, h.slot_bits + 4));
+        // Presence bitmap of 2^(slot_bits + 8) bits, 512 to 1024 per key (a
+        // probe of a non-key passes it with probability under 1/512), at most
+        // 2^16 bits.
+        h.bm_bits = std::min(16u, std::max(12u, h.slot_bits + 8));
     }
 
     // Layout.
@@ -638,6 +655,17 @@ uint32_t balanced_per(uint64_t units, uint32_t per) {
     return static_cast<uint32_t>((units + items - 1) / items);
 }
 
+// Units per item of one plan: `per`, lowered for q-gram plans so that a
+// warp's share of an item (32 thread ranges of tile_starts / threads starts
+// per unit) stays below 2^32 starts (the filter keeps warp-relative 32-bit
+// positions).
+uint32_t plan_per(const sm_plan *plan, uint32_t per) {
+    if (plan->kid != K_QGRAM) return per;
+    const uint64_t warp_unit = 32ull * (plan->hdr.tile_starts / qg_kernel_threads());
+    const uint64_t most = std::max<uint64_t>(1, 0xFFFFFFFFull / warp_unit);
+    return static_cast<uint32_t>(std::min<uint64_t>(per, most));
+}
+
 bool query_ok(const uint8_t *text, uint64_t n, const sm_plan *plan, const uint64_t *out_pos,
               uint64_t cap, const uint64_t *out_count) {
     if (!plan || !out_count || !aligned8(out_count)) return false;
@@ -721,7 +749,8 @@ sm_status search_plan_impl(const sm_plan *plan, const uint8_t *text, uint64_t n,
         SM_TRY_CUDA(cudaMemsetAsync(out_count, 0, sizeof(uint64_t), stream));
         return SM_OK;
     }
-    const uint32_t per = balanced_per(units, std::max(sub_per_item(plan->kid, units), plan->min_units));
+    const uint32_t per =
+        balanced_per(units, plan_per(plan, std::max(sub_per_item(plan->kid, units), plan->min_units)));
     const uint64_t ntiles = (units + per - 1) / per;
     const int grid = grid_for(plan->kid, ntiles);
     const size_t reset = align16(kTicketBytes + ntiles * sizeof(uint64_t));
@@ -846,7 +875,8 @@ sm_status batch_layout(const sm_query *qs, uint32_t nq, uint8_t *base, sm_batch 
     std::vector<uint32_t> per_q(nq, 1);
     for (uint32_t i = 0; i < nq; ++i) {
         if (units[i] == 0 || in_pack[i]) continue;
-        per_q[i] = balanced_per(units[i], std::max(group_per[qs[i].plan->kid], qs[i].plan->min_units));
+        per_q[i] = balanced_per(units[i], plan_per(qs[i].plan, std::max(group_per[qs[i].plan->kid],
+                                                                        qs[i].plan->min_units)));
         ntiles[i] = (units[i] + per_q[i] - 1) / per_q[i];
     }
     std::vector<uint32_t> per_pack(packs.size());

@@ -4,25 +4,38 @@
 // string-matching automaton (the AUT/DFA algorithm of the paper's tables).
 //
 // Filter (the Hash-q idea of Fig. 1, with q-grams compared exactly).  Let
-// s = m - q + 1.  Any occurrence [i, i+m-1] contains exactly one position
-// k*s in [i, i+m-q] (s consecutive integers hold one multiple of s), and
-// the q-gram of the text there equals p[j..j+q-1] for j = k*s - i.  So only
-// the text q-grams at multiples of s are looked up in the table of the
-// pattern's q-grams; each listed offset j gives one candidate i = k*s - j,
-// and every occurrence is produced exactly once.  Offsets are stored in
-// decreasing order, so each thread emits candidates in increasing order.
+// s = m - q + 1 and probe k sit at P_k = k*s + s - 1.  Any occurrence
+// [i, i+m-1] has its q-gram window [i, i+m-q] = [i, i+s-1], which holds
+// exactly one probe position (s consecutive integers hold one value
+// = s-1 mod s), that of k = floor(i/s); the q-gram of the text there equals
+// p[j..j+q-1] for j = P_k - i in [0, m-q].  So only the text q-grams at the
+// probe positions are looked up in the table of the pattern's q-grams; each
+// listed offset j gives one candidate i = P_k - j, and every occurrence is
+// produced exactly once, by the probe whose start range [k*s, k*s+s) holds
+// it.  Offsets are stored in decreasing order, so a probe's candidates come
+// out increasing, and consecutive probes cover consecutive start ranges.
 //
-// Verification: each lane first compares the first bytes of its own
-// candidate; surviving candidates of the warp are then checked one at a
-// time by all 32 lanes together (lane l compares bytes 16l..16l+15 of every
-// 512-byte block) with a ballot deciding the result.
+// Probes are interleaved over the lanes of a warp: in a round, lane l takes
+// probe k0 + l, so one warp load touches one contiguous stretch of text (a
+// stride of s bytes between lanes: every 32-byte sector when s < 32, about
+// one sector in s/32 when s is larger, which is where the filter reads less
+// than the whole text), and the warp's hits of a round come out in lane
+// order.  The q-grams of several rounds are loaded before the first of them
+// is looked up.  A probe first tests a presence bitmap; only rounds where
+// some lane passes it look the q-gram up in the hash table of exact keys.
 //
-// Density guard: a warp that spends more than a fixed number of verification
-// rounds per probe (periodic patterns on periodic text, e.g. a^m in a^n)
-// flags the tile, which is then recomputed with a linear scan per thread
-// over its start range plus m-1 bytes, O(range + m): the automaton (read
-// through the L1 cache) when the plan carries one -- periodic patterns, the
-// only ones that can occur densely -- else Knuth-Morris-Pratt.
+// Verification of a round: its candidates are staged in shared memory in
+// position order; each lane compares the first bytes of one candidate; the
+// survivors are checked one at a time by all 32 lanes together (lane l
+// compares bytes 16l..16l+15 of every 512-byte block) with a ballot deciding
+// the result.  The warp keeps its hits in order in shared memory.
+//
+// Density guard: a warp whose candidates exceed a fixed number per probe
+// (periodic patterns on periodic text, e.g. a^m in a^n) flags the work
+// item, which is then recomputed with a linear scan per thread over its
+// start range plus m-1 bytes, O(range + m): the automaton (read through the
+// L1 cache) when the plan carries one -- periodic patterns, the only ones
+// that can occur densely -- else Knuth-Morris-Pratt.
 //
 // Automaton.  delta(q, c) is the length of the longest prefix of p that is a
 // suffix of p[0..q-1] c (q = m after a match); the automaton started in
@@ -33,10 +46,11 @@
 // is two shared loads (class, then transition) and one add, the same for
 // every m.
 //
-// Compaction is the same as in the bit-parallel kernel: per-thread counts,
-// block scan, decoupled look-back, ordered writes.  Per-thread hits are
-// buffered in shared memory; a thread with more hits than the buffer holds
-// recomputes its range in write mode once its output offset is known.
+// Compaction is the same as in the bit-parallel kernel: per-warp (filter) or
+// per-thread (linear scans) counts, block scan, decoupled look-back, ordered
+// writes.  Hits are kept in shared memory; a warp or thread with more hits
+// than its buffer holds recomputes its range in write mode once its output
+// offset is known.
 #include "sm_internal.h"
 
 namespace smgpu {
@@ -44,8 +58,17 @@ namespace smgpu {
 namespace {
 
 constexpr int QG_THREADS = 128;
-constexpr int QG_HB = 8;              // buffered hits per thread
-constexpr int QG_ROUNDS_PER_PROBE = 4; // density guard budget (warp rounds per probe)
+constexpr int QG_HB = 8;              // buffered hits per thread (linear scans)
+constexpr int QG_ROUNDS_PER_PROBE = 4; // density guard budget (candidates per probe)
+constexpr int QG_WL = 512;            // hits a warp keeps in shared memory per work item
+constexpr int QG_CB = 128;            // candidates of one probe round staged by a warp
+constexpr int QG_U = 4;               // probe rounds whose q-grams are loaded ahead
+
+// Per-warp shared state of the q-gram filter.
+struct QGWarp {
+    uint32_t list[QG_WL];  // hits, relative to the warp's first start
+    uint32_t cand[QG_CB];  // candidates of the current round (relative), or ~0u
+};
 
 // Kernel families built from this file.
 enum : int { QG_QGRAM = 0, QG_KMP = 1, QG_DFA = 2 };
@@ -119,11 +142,10 @@ __device__ __forceinline__ uint32_t dfa_step(const DfaView &d, uint32_t r, uint3
     return __ldg(reinterpret_cast<const uint16_t *>(d.tab + r + __ldg(d.cls + c)));
 }
 
-// Looks up q-gram g; returns the number of offsets and their first index.
+// Looks up q-gram g (whose bitmap bit is set) in the table of exact keys;
+// returns the number of offsets and their first index (0: not a key).
 __device__ __forceinline__ uint32_t qgram_lookup(const PlanView &v, uint64_t g, uint32_t *first) {
     const uint64_t h = qgram_hash(g);
-    const uint32_t hb = static_cast<uint32_t>(h >> (64u - v.bm_bits));
-    if (!((__ldg(&v.bitmap[hb >> 5]) >> (hb & 31u)) & 1u)) return 0;
     const uint32_t mask = (1u << v.slot_bits) - 1u;
     uint32_t sl = static_cast<uint32_t>(h >> (64u - v.slot_bits));
     while (true) {
@@ -228,51 +250,141 @@ struct VSink {
     }
 };
 
-// q-gram filter over start range [L, min(L+R, n-m+1)).  All lanes of the
-// warp must call it with the same R (trip counts agree).  Returns false if
-// the warp exceeded the verification budget (count mode only).
-__device__ bool qgram_range(const PlanView &v, const uint8_t *text, uint64_t n, uint64_t L,
-                            uint64_t R, Sink &sink, bool guard) {
+// Exclusive warp scan of v (whole warp); *total receives the warp's sum.
+__device__ __forceinline__ uint32_t qg_warp_scan(uint32_t v, uint32_t *total) {
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= static_cast<uint32_t>(d)) x += y;
+    }
+    *total = __shfl_sync(0xffffffffu, x, 31);
+    return x - v;
+}
+
+// Filter state a warp carries across its probe rounds.
+struct QGRun {
+    uint64_t ncand;  // candidates staged so far (density guard)
+    uint32_t cnt;    // hits so far
+    uint32_t ovf;    // 1: more hits than the warp's list holds
+};
+
+// Output side of a warp's filter run: the count pass keeps hits in ws.list,
+// the write pass stores them at out[base + rank] (ranks below cap).
+struct QGOut {
+    QGWarp *ws;
+    uint64_t *out;
+    uint64_t cap;
+    uint64_t base;
+    uint32_t write;
+};
+
+// One probe round that some lane's bitmap test passed: exact keys (the
+// q-gram at P is loaded again, so the probe loop keeps no q-gram alive past
+// its bitmap test), this round's candidates staged in position order,
+// prefix check one candidate per lane, full check of the survivors by the
+// whole warp, hits in order.  Returns false if the count pass exceeds the
+// density budget or stages more than QG_CB candidates.
+__device__ __forceinline__ bool qgram_round(const PlanView &v, uint64_t patw, const uint8_t *text, uint64_t n,
+                                            uint64_t Lw, bool hit, uint64_t P, uint64_t budget,
+                                            const QGOut &o, QGRun &run) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t pre = min(v.m, 8u);
+    uint32_t first = 0, c = 0;
+    if (hit) c = qgram_lookup(v, load_qgram(text, P, v.q), &first);
+    uint32_t tot;
+    const uint32_t ex = qg_warp_scan(c, &tot);
+    if (tot == 0) return true;
+    run.ncand += tot;
+    if (tot > static_cast<uint32_t>(QG_CB) || (!o.write && run.ncand > budget)) return false;
+    QGWarp &ws = *o.ws;
+    for (uint32_t t = 0; t < c; ++t) {
+        const uint64_t i = P - __ldg(&v.offs[first + t]);
+        ws.cand[ex + t] = i <= n - v.m ? static_cast<uint32_t>(i - Lw) : ~0u;
+    }
+    __syncwarp();
+    for (uint32_t c0 = 0; c0 < tot; c0 += 32) {
+        const uint32_t ci = c0 + lane;
+        const uint32_t rel = ci < tot ? ws.cand[ci] : ~0u;
+        const bool keep = rel != ~0u && load_qgram(text, Lw + rel, pre) == patw;
+        unsigned km = __ballot_sync(0xffffffffu, keep);
+        while (km) {
+            const int src = __ffs(km) - 1;
+            km &= km - 1u;
+            const uint32_t rs = __shfl_sync(0xffffffffu, rel, src);
+            if (!warp_equal(text + Lw + rs, v.pat, v.m)) continue;
+            if (o.write) {
+                if (lane == 0 && o.base + run.cnt < o.cap) o.out[o.base + run.cnt] = Lw + rs;
+            } else if (run.cnt < static_cast<uint32_t>(QG_WL)) {
+                if (lane == 0) ws.list[run.cnt] = rs;
+            } else {
+                run.ovf = 1u;
+            }
+            ++run.cnt;
+        }
+    }
+    __syncwarp();  // the next round rewrites the candidates
+    return true;
+}
+
+// The q-gram filter of one warp over the start range [Lw, Lw + span) (Lw
+// and span multiples of s; span < 2^32), in probe rounds of 32 probes (lane
+// l takes the l-th).  Hits go, in increasing order, to the warp's list
+// (count pass; run.ovf set when more than QG_WL were found) or straight to
+// the output (write pass).  Returns false if the count pass exceeded the
+// density budget: the work item is then recomputed linearly.  Whole warp,
+// warp-uniform arguments.
+__device__ bool qgram_warp(const PlanView &v, uint64_t patw, const uint8_t *text, uint64_t n, uint64_t Lw,
+                           uint64_t span, const QGOut &o, QGRun &run) {
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t s = v.s;
-    const uint64_t hi = min(L + R, n - v.m + 1);  // exclusive; L may be >= hi
-    const uint64_t k0 = L / s;                     // L is a multiple of s
-    const uint64_t probes = R / s + 1;
-    const uint32_t pre = min(v.m, 8u);
-    uint64_t rounds = 0;
-    const uint64_t budget = static_cast<uint64_t>(QG_ROUNDS_PER_PROBE) * probes + 32;
-    for (uint64_t pk = 0; pk < probes; ++pk) {
-        const uint64_t pos = (k0 + pk) * s;
-        uint32_t first = 0, count = 0;
-        if (L < hi && pos + v.q <= n) count = qgram_lookup(v, load_qgram(text, pos, v.q), &first);
-        uint32_t c = 0;
-        while (true) {
-            // Next candidate of this lane that lies in range and passes the
-            // prefix check.
-            uint64_t cand = 0;
-            bool have = false;
-            while (c < count) {
-                const uint64_t j = __ldg(&v.offs[first + c]);
-                ++c;
-                if (pos < j) continue;
-                const uint64_t i = pos - j;
-                if (i < L) continue;
-                if (i >= hi) { c = count; break; }
-                bool eq = true;
-                for (uint32_t b = 0; b < pre; ++b) eq &= __ldg(text + i + b) == __ldg(v.pat + b);
-                if (eq) { cand = i; have = true; break; }
-            }
-            unsigned mask = __ballot_sync(0xffffffffu, have);
-            if (!mask) break;
-            rounds += __popc(mask);
-            if (guard && rounds > budget) return false;
-            while (mask) {
-                const int src = __ffs(mask) - 1;
-                mask &= mask - 1u;
-                const uint64_t ic = __shfl_sync(0xffffffffu, cand, src);
-                const bool eq = warp_equal(text + ic, v.pat, v.m);
-                if (eq && lane == static_cast<uint32_t>(src)) sink.put(cand, L);
-            }
+    const uint64_t k0 = Lw / s;
+    const uint64_t kend = min(k0 + span / s, (n - v.m) / s + 1);  // probes [k0, kend) hold valid starts
+    const uint64_t nr = kend > k0 ? (kend - k0 + 31) / 32 : 0;
+    const uint64_t budget = static_cast<uint64_t>(QG_ROUNDS_PER_PROBE) * 32u * nr + 32u;
+    const uint64_t qmask = v.q >= 8 ? ~0ull : ((1ull << (8u * v.q)) - 1ull);
+    run = QGRun{0, 0, 0};
+    for (uint64_t r0 = 0; r0 < nr; r0 += QG_U) {
+        // Every load of the QG_U rounds is issued before any of their words
+        // is used: the two aligned words that hold each probe's q-gram (the
+        // second only when the q-gram reaches into it), then the bitmap
+        // words; one vote decides whether any of the rounds needs the table.
+        uint64_t lo[QG_U], hi[QG_U];
+        uint32_t sh[QG_U];
+#pragma unroll
+        for (int u = 0; u < QG_U; ++u) {
+            const uint64_t kp = k0 + (r0 + u) * 32u + lane;
+            const bool live = kp < kend;
+            const uintptr_t addr = reinterpret_cast<uintptr_t>(text) + (live ? kp * s + s - 1u : 0u);
+            const uint64_t *w = reinterpret_cast<const uint64_t *>(addr & ~uintptr_t(7));
+            sh[u] = static_cast<uint32_t>(addr & 7u);
+            lo[u] = live ? __ldg(w) : 0ull;
+            hi[u] = live && sh[u] + v.q > 8u ? __ldg(w + 1) : 0ull;
+        }
+        uint64_t g[QG_U];
+        uint32_t bw[QG_U], bb[QG_U];
+#pragma unroll
+        for (int u = 0; u < QG_U; ++u) {
+            const uint32_t b = 8u * sh[u];
+            g[u] = (b ? (lo[u] >> b) | (hi[u] << (64u - b)) : lo[u]) & qmask;
+            const uint32_t hb = static_cast<uint32_t>(qgram_hash(g[u]) >> (64u - v.bm_bits));
+            bb[u] = hb & 31u;
+            bw[u] = __ldg(&v.bitmap[hb >> 5]);
+        }
+        uint32_t hits = 0;  // bit u: round u passes the bitmap on this lane
+#pragma unroll
+        for (int u = 0; u < QG_U; ++u) {
+            const uint64_t kp = k0 + (r0 + u) * 32u + lane;
+            hits |= (kp < kend && ((bw[u] >> bb[u]) & 1u)) ? (1u << u) : 0u;
+        }
+        if (!__any_sync(0xffffffffu, hits != 0)) continue;
+#pragma unroll 1
+        for (int u = 0; u < QG_U; ++u) {
+            const bool hit = (hits >> u) & 1u;
+            if (!__any_sync(0xffffffffu, hit)) continue;
+            const uint64_t kp = k0 + (r0 + u) * 32u + lane;
+            if (!qgram_round(v, patw, text, n, Lw, hit, kp * s + s - 1u, budget, o, run)) return false;
         }
     }
     return true;
@@ -364,6 +476,8 @@ __global__ void __launch_bounds__(QG_THREADS) qg_kernel(const LaunchArgs a) {
     __shared__ QGCtl ctl;
     __shared__ uint32_t hbuf[QG_HB * QG_THREADS];
     __shared__ __align__(16) uint8_t dfa_raw[MODE == QG_DFA ? sizeof(DfaShared) : 16];
+    __shared__ __align__(16) uint8_t qgw_raw[MODE == QG_QGRAM ? sizeof(QGWarp) * (QG_THREADS / 32) : 16];
+    QGWarp *qgw = reinterpret_cast<QGWarp *>(qgw_raw);
     DfaShared &dsm = *reinterpret_cast<DfaShared *>(dfa_raw);
     const PlanDev *loaded = nullptr;  // plan whose automaton is in shared memory
     const int tid = threadIdx.x;
@@ -423,11 +537,23 @@ __global__ void __launch_bounds__(QG_THREADS) qg_kernel(const LaunchArgs a) {
             else linear_range(v, text, n, L, R, sk);
         };
 
-        // ---- count pass (q-gram filter, or linear scan for dense tiles)
+        // ---- count pass (q-gram filter per warp, or linear scan per thread
+        // for dense items).  The filter of warp w covers the starts of its
+        // 32 threads' ranges, [Lw, Lw + 32 R).
         Sink sink{SINK_BUFFER, nullptr, 0, 0, hbuf + tid, 0};
+        const uint64_t Lw = k * R * QG_THREADS + static_cast<uint64_t>(warp) * 32u * R;
+        uint64_t patw = 0;
+        uint32_t wcnt = 0;
+        bool wovf = false;
         if (MODE == QG_QGRAM) {
-            const bool fine = qgram_range(v, text, n, L, R, sink, true);
-            if (!__all_sync(0xffffffffu, fine) && lane == 0) ctl.dense = 1u;
+            const uint32_t pre = min(v.m, 8u);
+            patw = *reinterpret_cast<const uint64_t *>(v.pat);  // 16-byte aligned, zero padded
+            if (pre < 8) patw &= (1ull << (8u * pre)) - 1ull;
+            QGRun run;
+            const bool fine = qgram_warp(v, patw, text, n, Lw, 32u * R, QGOut{&qgw[warp], nullptr, 0, 0, 0u}, run);
+            wcnt = run.cnt;
+            wovf = run.ovf != 0;
+            if (!fine && lane == 0) ctl.dense = 1u;
         }
         __syncthreads();
         const bool dense = ctl.dense != 0;
@@ -435,7 +561,9 @@ __global__ void __launch_bounds__(QG_THREADS) qg_kernel(const LaunchArgs a) {
             sink.cnt = 0;
             linear(sink);
         }
-        const uint32_t cnt = sink.cnt;
+        // Sparse q-gram items: the warp's total stands on its lane 0, so the
+        // block scan below yields the warp's output offset there.
+        const uint32_t cnt = dense ? sink.cnt : (lane == 0 ? wcnt : 0u);
 
         // ---- block scan + look-back
         uint32_t x = cnt;
@@ -469,20 +597,33 @@ __global__ void __launch_bounds__(QG_THREADS) qg_kernel(const LaunchArgs a) {
         // ---- write pass
         if (ctl.ok) {
             const uint64_t base = ctl.excl + ctl.warp_ex[warp] + (x - cnt);
-            const bool over = cnt > QG_HB;
-            if (!over) {
-                for (uint32_t r = 0; r < cnt; ++r) {
-                    const uint64_t idx = base + r;
-                    if (idx < Q.cap) Q.out_pos[idx] = L + hbuf[r * QG_THREADS + tid];
-                }
-            }
-            // Threads whose hits did not fit recompute their range in write
-            // mode; the whole warp joins when the q-gram path needs it.
-            Sink w{over ? SINK_WRITE : SINK_DISCARD, Q.out_pos, Q.cap, base, nullptr, 0};
             if (dense) {
-                if (over) linear(w);
-            } else if (__any_sync(0xffffffffu, over)) {
-                qgram_range(v, text, n, L, R, w, false);
+                const bool over = cnt > QG_HB;
+                if (!over) {
+                    for (uint32_t r = 0; r < cnt; ++r) {
+                        const uint64_t idx = base + r;
+                        if (idx < Q.cap) Q.out_pos[idx] = L + hbuf[r * QG_THREADS + tid];
+                    }
+                } else {
+                    // Threads whose hits did not fit recompute their range
+                    // in write mode.
+                    Sink w{SINK_WRITE, Q.out_pos, Q.cap, base, nullptr, 0};
+                    linear(w);
+                }
+            } else if (MODE == QG_QGRAM) {
+                const uint64_t bw = __shfl_sync(0xffffffffu, base, 0);
+                if (!wovf) {
+                    const uint64_t cap = Q.cap;
+                    uint64_t *out = Q.out_pos;
+                    for (uint32_t r = lane; r < wcnt; r += 32) {
+                        if (bw + r < cap) out[bw + r] = Lw + qgw[warp].list[r];
+                    }
+                } else {
+                    // More hits than the warp's list holds: run the filter
+                    // again, writing at the final offsets.
+                    QGRun run;
+                    qgram_warp(v, patw, text, n, Lw, 32u * R, QGOut{&qgw[warp], Q.out_pos, Q.cap, bw, 1u}, run);
+                }
             }
         }
         __syncthreads();

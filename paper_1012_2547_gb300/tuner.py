@@ -6,11 +6,13 @@ pattern length and alphabet size.  The library therefore keeps a table of
 configurations indexed by the bucket of m (floor(log2 m), 0..11) and of
 sigma (0 = unknown, else floor(log2 sigma) clamped to 1..8), used by
 sm_prepare when no explicit configuration is given (include/smgpu.h,
-sm_tuning_*).  This module fills that table by timing every candidate
-configuration (Shift-Or with a 32- or 64-bit state, q-gram filter for
-q in {3, ..., 8}) on a batch of substring patterns of a uniform text of
-each alphabet size, as one graph-captured batch per candidate, and keeping
-the fastest.  The table can be saved to and loaded from JSON.
+sm_tuning_*).  This module fills that table by timing candidate
+configurations on a batch of substring patterns of a uniform text of each
+alphabet size, as one graph-captured batch per candidate, and keeping the
+fastest: first every kernel family and its parameter (Shift-Or with a 32-
+or 64-bit state, q-gram filter for q in {3, ..., 8}, the automaton where
+its table fits), then the work-item size (the `tile` field) of the
+fastest.  The table can be saved to and loaded from JSON.
 """
 from __future__ import annotations
 
@@ -26,7 +28,12 @@ from . import Batch, _lib, gen, prepare_many, search_batch, sync, tuning_get, tu
 
 M_BUCKETS = _lib.TUNE_M_BUCKETS
 S_BUCKETS = _lib.TUNE_S_BUCKETS
-VARIANT_IDS = {"shiftor": 1, "qgram": 2, "linear": 3}
+VARIANT_IDS = {"shiftor": 1, "qgram": 2, "linear": 3, "dfa": 4}
+DFA_MAX_TABLE = 32768 - 256  # the library's bound on an automaton's table (bytes)
+# Work-item sizes tried for the fastest family (log2 bytes; 0 = the
+# library's default): Shift-Or: shortest work item; q-gram and automaton:
+# start positions per thread range.
+TILES = {"shiftor": (0, 17, 19), "qgram": (0, 11, 14), "dfa": (0, 12), "linear": (0,)}
 
 
 def m_bucket(m: int) -> int:
@@ -43,19 +50,24 @@ def s_bucket(sigma: int) -> int:
 
 def builtin(m: int, sigma: int = 0) -> dict:
     """The library's built-in choice for length m on an alphabet of sigma
-    (tuning cell variant 0): Shift-Or up to m = 64, else the q-gram filter
-    with q = ceil(log(64 m) / log sigma) clamped to 3..8 (sigma 4 when
-    unknown)."""
-    if m <= 32:
-        return {"variant": "shiftor", "word_bits": 32}
-    if m <= 64:
-        return {"variant": "shiftor", "word_bits": 64}
+    (tuning cell variant 0): Shift-Or up to m = 16, and up to m = 64 when
+    sigma is 2 or 3; else the q-gram filter with the smallest q such that
+    sigma**q >= 2**11 * m, clamped to 3..8 (sigma 4 when unknown)."""
+    if m <= 16 or (m <= 64 and sigma in (2, 3)):
+        return {"variant": "shiftor", "word_bits": 32 if m <= 32 else 64}
     sg = sigma if sigma >= 2 else 4
-    q = min(8, max(3, math.ceil(math.log(64.0 * m) / math.log(sg))))
+    q = min(8, max(3, math.ceil(math.log(2048.0 * m) / math.log(sg) - 1e-9)))
     return {"variant": "qgram", "q": min(q, m)}
 
 
-def candidates(m: int) -> list[dict]:
+def dfa_fits(p: bytes) -> bool:
+    """The automaton of p has (m+1) x C two-byte entries, C = distinct bytes + 1."""
+    return (len(p) + 1) * (len(set(p)) + 1) * 2 <= DFA_MAX_TABLE
+
+
+def candidates(m: int, patterns=None) -> list[dict]:
+    """Kernel families (with their parameter) able to serve length m; the
+    automaton only when every given pattern's table fits."""
     out = []
     if m <= 32:
         out.append({"variant": "shiftor", "word_bits": 32})
@@ -64,7 +76,15 @@ def candidates(m: int) -> list[dict]:
     for q in (3, 4, 5, 6, 7, 8):
         if q <= m and m - q + 1 >= 2:
             out.append({"variant": "qgram", "q": q})
+    if patterns is not None and patterns and all(dfa_fits(p) for p in patterns):
+        out.append({"variant": "dfa"})
     return out
+
+
+def cfg_key(cfg: dict) -> str:
+    v = cfg["variant"]
+    k = v + (f"{cfg.get('word_bits')}" if v == "shiftor" else f"q{cfg.get('q')}" if v == "qgram" else "")
+    return k + (f"t{cfg['tile']}" if cfg.get("tile") else "")
 
 
 def _time_batch(text, pats, sigma, cfg, reps, flush):
@@ -125,10 +145,13 @@ def tune(sigmas=(2, 4, 8, 16, 32, 64, 128), ms=gen.SWEEP_M, n: int = 4 << 20, pe
             offs = gen.pattern_offsets(n, m, per, seed * 7 + m)
             pats = [bytes(spec.window(o, m)) for o in offs]
             res = {}
-            for cfg in candidates(m):
-                key = cfg["variant"] + (f"{cfg.get('word_bits')}" if cfg["variant"] == "shiftor"
-                                        else f"q{cfg.get('q')}")
-                res[key] = (_time_batch(text, pats, sigma, cfg, reps, flush), cfg)
+            for cfg in candidates(m, pats):
+                res[cfg_key(cfg)] = (_time_batch(text, pats, sigma, cfg, reps, flush), cfg)
+            # Work-item sizes of the fastest family.
+            top = res[min(res, key=lambda k: res[k][0])][1]
+            for tile in TILES[top["variant"]][1:]:
+                cfg = dict(top, tile=tile)
+                res[cfg_key(cfg)] = (_time_batch(text, pats, sigma, cfg, reps, flush), cfg)
             best_key = min(res, key=lambda k: res[k][0])
             b = builtin(m, sigma)
             b_key = next((k for k, v in res.items() if v[1] == b), None)
@@ -137,7 +160,7 @@ def tune(sigmas=(2, 4, 8, 16, 32, 64, 128), ms=gen.SWEEP_M, n: int = 4 << 20, pe
             best_t, best_cfg = res[best_key]
             idx = m_bucket(m) * S_BUCKETS + s_bucket(sigma)
             cells[idx] = {"variant": VARIANT_IDS[best_cfg["variant"]], "q": best_cfg.get("q", 0),
-                          "word_bits": best_cfg.get("word_bits", 0), "tile": 0}
+                          "word_bits": best_cfg.get("word_bits", 0), "tile": best_cfg.get("tile", 0)}
             row = {"sigma": sigma, "m": m, "best": best_key,
                    "gbs": {k: round(per * n / v[0] / 1e9, 1) for k, v in res.items()}}
             report.append(row)

@@ -53,7 +53,7 @@ def test_committed_gb300_table_loads():
     r = tuner.load(tuner.GB300_TABLE, apply=False)
     assert len(r["cells"]) == tuner.M_BUCKETS * tuner.S_BUCKETS
     for c in r["cells"]:
-        assert c["variant"] in (0, 1, 2, 3)
+        assert c["variant"] in (0, 1, 2, 3, 4)
         if c["variant"] == 2:
             assert 1 <= c["q"] <= 8
     with open(tuner.GB300_TABLE) as f:
@@ -63,8 +63,11 @@ def test_committed_gb300_table_loads():
 def test_builtin_choice_rule():
     from paper_1012_2547_gb300 import tuner
     assert tuner.builtin(8)["variant"] == "shiftor" and tuner.builtin(8)["word_bits"] == 32
-    assert tuner.builtin(40)["word_bits"] == 64
-    assert tuner.builtin(100, 4) == {"variant": "qgram", "q": 7}      # ceil(log 6400 / log 4)
+    assert tuner.builtin(16, 4)["variant"] == "shiftor"
+    assert tuner.builtin(40, 2) == {"variant": "shiftor", "word_bits": 64}
+    assert tuner.builtin(32, 4) == {"variant": "qgram", "q": 8}       # 4**8 = 2**11 * 32
+    assert tuner.builtin(40) == {"variant": "qgram", "q": 8}          # unknown sigma counts as 4
+    assert tuner.builtin(100, 20) == {"variant": "qgram", "q": 5}     # ceil(log 204800 / log 20)
     assert tuner.builtin(1024, 128) == {"variant": "qgram", "q": 3}
     assert tuner.builtin(1024, 2) == {"variant": "qgram", "q": 8}
     for m in (8, 40, 100, 1024):

@@ -24,13 +24,14 @@
 // is looked up.  A probe first tests a presence bitmap; only rounds where
 // some lane passes it look the q-gram up in the hash table of exact keys.
 //
-// Verification of a round: its candidates are staged in shared memory in
-// position order; each lane compares the first bytes of one candidate; the
-// survivors are checked one at a time by all 32 lanes together (lane l
-// compares bytes 16l..16l+15 of every 512-byte block) with a ballot deciding
-// the result.  The warp keeps its hits in order in shared memory.
+// Verification of a round: each lane walks its own candidates in order and
+// compares their first bytes; the survivors are checked in lane order, one
+// at a time, by all 32 lanes together (lane l compares bytes 16l..16l+15 of
+// every 512-byte block) with a ballot deciding the result.  The warp keeps
+// its hits in order in shared memory.
 //
-// Density guard: a warp whose candidates exceed a fixed number per probe
+// Density guard: a warp whose fully checked candidates exceed a fixed number
+// per probe
 // (periodic patterns on periodic text, e.g. a^m in a^n) flags the work
 // item, which is then recomputed with a linear scan per thread over its
 // start range plus m-1 bytes, O(range + m): the automaton (read through the
@@ -61,13 +62,11 @@ constexpr int QG_THREADS = 128;
 constexpr int QG_HB = 8;              // buffered hits per thread (linear scans)
 constexpr int QG_ROUNDS_PER_PROBE = 4; // density guard budget (candidates per probe)
 constexpr int QG_WL = 512;            // hits a warp keeps in shared memory per work item
-constexpr int QG_CB = 128;            // candidates of one probe round staged by a warp
 constexpr int QG_U = 4;               // probe rounds whose q-grams are loaded ahead
 
 // Per-warp shared state of the q-gram filter.
 struct QGWarp {
     uint32_t list[QG_WL];  // hits, relative to the warp's first start
-    uint32_t cand[QG_CB];  // candidates of the current round (relative), or ~0u
 };
 
 // Kernel families built from this file.
@@ -265,7 +264,7 @@ __device__ __forceinline__ uint32_t qg_warp_scan(uint32_t v, uint32_t *total) {
 
 // Filter state a warp carries across its probe rounds.
 struct QGRun {
-    uint64_t ncand;  // candidates staged so far (density guard)
+    uint64_t ncand;  // candidates fully checked so far (density guard)
     uint32_t cnt;    // hits so far
     uint32_t ovf;    // 1: more hits than the warp's list holds
 };
@@ -280,51 +279,59 @@ struct QGOut {
     uint32_t write;
 };
 
-// One probe round that some lane's bitmap test passed: exact keys (the
-// q-gram at P is loaded again, so the probe loop keeps no q-gram alive past
-// its bitmap test), this round's candidates staged in position order,
-// prefix check one candidate per lane, full check of the survivors by the
-// whole warp, hits in order.  Returns false if the count pass exceeds the
-// density budget or stages more than QG_CB candidates.
+// One probe round that some lane's bitmap test passed.  Each such lane
+// looks its q-gram up in the table of exact keys (loading it again, so the
+// probe loop keeps no q-gram alive past its bitmap test) and walks its
+// candidates in increasing order, comparing the first min(m, 8) bytes; the
+// survivors are checked one at a time by the whole warp, the lowest lane's
+// first, and only that lane moves on to its next survivor, so hits come out
+// in lane order and, within a lane, in increasing order.  Returns false if
+// the count pass exceeds the density budget (full checks per probe).
 __device__ __forceinline__ bool qgram_round(const PlanView &v, uint64_t patw, const uint8_t *text, uint64_t n,
                                             uint64_t Lw, bool hit, uint64_t P, uint64_t budget,
                                             const QGOut &o, QGRun &run) {
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t pre = min(v.m, 8u);
-    uint32_t first = 0, c = 0;
+    const uint64_t last = n - v.m;  // last valid start
+    uint32_t first = 0, c = 0, t = 0;
     if (hit) c = qgram_lookup(v, load_qgram(text, P, v.q), &first);
-    uint32_t tot;
-    const uint32_t ex = qg_warp_scan(c, &tot);
-    if (tot == 0) return true;
-    run.ncand += tot;
-    if (tot > static_cast<uint32_t>(QG_CB) || (!o.write && run.ncand > budget)) return false;
-    QGWarp &ws = *o.ws;
-    for (uint32_t t = 0; t < c; ++t) {
-        const uint64_t i = P - __ldg(&v.offs[first + t]);
-        ws.cand[ex + t] = i <= n - v.m ? static_cast<uint32_t>(i - Lw) : ~0u;
-    }
-    __syncwarp();
-    for (uint32_t c0 = 0; c0 < tot; c0 += 32) {
-        const uint32_t ci = c0 + lane;
-        const uint32_t rel = ci < tot ? ws.cand[ci] : ~0u;
-        const bool keep = rel != ~0u && load_qgram(text, Lw + rel, pre) == patw;
-        unsigned km = __ballot_sync(0xffffffffu, keep);
-        while (km) {
-            const int src = __ffs(km) - 1;
-            km &= km - 1u;
-            const uint32_t rs = __shfl_sync(0xffffffffu, rel, src);
-            if (!warp_equal(text + Lw + rs, v.pat, v.m)) continue;
+    uint64_t cand = 0;
+    // Next candidate of this lane that passes the prefix comparison.
+    auto advance = [&]() -> bool {
+        while (t < c) {
+            const uint64_t i = P - __ldg(&v.offs[first + t]);
+            ++t;
+            if (i > last) {  // offsets descend, so every later candidate is past the end too
+                t = c;
+                break;
+            }
+            if (load_qgram(text, i, pre) == patw) {
+                cand = i;
+                return true;
+            }
+        }
+        return false;
+    };
+    bool have = advance();
+    while (true) {
+        const unsigned mask = __ballot_sync(0xffffffffu, have);
+        if (!mask) break;
+        const int src = __ffs(mask) - 1;
+        const uint64_t ic = __shfl_sync(0xffffffffu, cand, src);
+        if (!o.write && ++run.ncand > budget) return false;
+        if (warp_equal(text + ic, v.pat, v.m)) {
+            const uint32_t rs = static_cast<uint32_t>(ic - Lw);
             if (o.write) {
-                if (lane == 0 && o.base + run.cnt < o.cap) o.out[o.base + run.cnt] = Lw + rs;
+                if (lane == 0 && o.base + run.cnt < o.cap) o.out[o.base + run.cnt] = ic;
             } else if (run.cnt < static_cast<uint32_t>(QG_WL)) {
-                if (lane == 0) ws.list[run.cnt] = rs;
+                if (lane == 0) o.ws->list[run.cnt] = rs;
             } else {
                 run.ovf = 1u;
             }
             ++run.cnt;
         }
+        if (lane == static_cast<uint32_t>(src)) have = advance();
     }
-    __syncwarp();  // the next round rewrites the candidates
     return true;
 }
 

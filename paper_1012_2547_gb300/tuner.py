@@ -33,7 +33,7 @@ DFA_MAX_TABLE = 32768 - 256  # the library's bound on an automaton's table (byte
 # Work-item sizes tried for the fastest family (log2 bytes; 0 = the
 # library's default): Shift-Or: shortest work item; q-gram and automaton:
 # start positions per thread range.
-TILES = {"shiftor": (0, 17, 19), "qgram": (0, 11, 14), "dfa": (0, 12), "linear": (0,)}
+TILES = {"shiftor": (0, 17, 19), "qgram": (0, 11, 14, 16), "dfa": (0, 12), "linear": (0,)}
 
 
 def m_bucket(m: int) -> int:

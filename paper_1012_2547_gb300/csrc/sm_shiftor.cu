@@ -102,6 +102,23 @@ lds_entry(uint32_t addr) {
     }
 }
 
+// Signed byte at shared address `addr`: bits 8..31 copy bit 7.
+__device__ __forceinline__ uint32_t lds_s8(uint32_t addr) {
+    int32_t v;
+    asm volatile("ld.shared.s8 %0, [%1];" : "=r"(v) : "r"(addr));
+    return static_cast<uint32_t>(v);
+}
+
+// Run-time constants of the scan steps: values the compiler cannot fold, so
+// that the state's shift stays an IMAD on the FMA pipe.
+struct SOK {
+    uint32_t tb;    // shared address of the mask table (256-aligned)
+    uint32_t tb1;   // pair step: shared address of the shifted-mask table (256-aligned)
+    uint32_t two;   // 2
+    uint32_t four;  // 4
+    uint32_t esz;   // bytes per table entry
+};
+
 // Table entry of byte b of word x, widened to the state (zero above the
 // entry's own bits).  `tb` is the table's shared address, 256-aligned: for
 // byte entries one PRMT puts the text byte under tb's upper bytes, which is
@@ -138,11 +155,29 @@ __device__ __forceinline__ Word so_update(Word D, Word e, uint32_t two) {
     return (D2 & e) | (K & (D2 | e));
 }
 
-template <typename Word, typename Entry>
-__device__ __forceinline__ void so_step4(Word &D, uint32_t x, uint32_t tb, uint32_t two,
-                                         uint32_t esz) {
+// Four steps on the bytes of x.  PAIR (byte tables, m <= 6, 32-bit state):
+// two bytes per step.  Composing two steps,
+//   D <- ((D << 2) | 3) & B1[c1] & B[c2],   B1[c] = (B[c] << 1) | 1,
+// where both tables hold one byte per entry with every bit >= m of B (and
+// >= m+1 of B1) set; for m <= 6 bit 7 of both is set, so a sign-extending
+// load supplies the ones above the byte and one 3-input AND finishes the
+// step: per two bytes two PRMT, two loads, one IMAD and one LOP3 instead of
+// twice four instructions.
+template <typename Word, typename Entry, bool PAIR>
+__device__ __forceinline__ void so_step4(Word &D, uint32_t x, const SOK &k) {
+    if constexpr (PAIR) {
+        static_assert(sizeof(Word) == 4 && sizeof(Entry) == 1, "pair steps use byte tables and a 32-bit state");
 #pragma unroll
-    for (int b = 0; b < 4; ++b) D = so_update<Word, Entry>(D, so_entry_b<Word, Entry>(x, b, tb, esz), two);
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t e1 = lds_s8(__byte_perm(x, k.tb1, 0x7650u | (2 * h)));
+            const uint32_t e2 = lds_s8(__byte_perm(x, k.tb, 0x7650u | (2 * h + 1)));
+            D = (static_cast<uint32_t>(D) * k.four + 3u) & e1 & e2;
+        }
+    } else {
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+            D = so_update<Word, Entry>(D, so_entry_b<Word, Entry>(x, b, k.tb, k.esz), k.two);
+    }
 }
 
 // Exact flags of one 16-byte chunk (bit 15-b <=> an occurrence ends at byte
@@ -171,17 +206,17 @@ __device__ __forceinline__ uint32_t range_mask16(int cb, int elo, int ehi) {
 // Local scan of one lane segment from the empty state.  F[c] bit r flags an
 // occurrence ending at segment byte 16c + 15 - r; returns the final state,
 // which is exact because the segment is at least m bytes long.
-template <typename Word, typename Entry, bool HIST>
-__device__ __forceinline__ Word so_local(const uint8_t *seg, Word D, uint32_t tb, uint32_t m,
-                                         uint32_t two, uint32_t esz, uint32_t (&F)[SO_SEGC]) {
+template <typename Word, typename Entry, bool HIST, bool PAIR>
+__device__ __forceinline__ Word so_local(const uint8_t *seg, Word D, const SOK &k, uint32_t m,
+                                         uint32_t (&F)[SO_SEGC]) {
 #pragma unroll
     for (int c = 0; c < SO_SEGC; ++c) {
         const uint4 w = *reinterpret_cast<const uint4 *>(seg + 16 * c);
         if (HIST) {
-            so_step4<Word, Entry>(D, w.x, tb, two, esz);
-            so_step4<Word, Entry>(D, w.y, tb, two, esz);
-            so_step4<Word, Entry>(D, w.z, tb, two, esz);
-            so_step4<Word, Entry>(D, w.w, tb, two, esz);
+            so_step4<Word, Entry, PAIR>(D, w.x, k);
+            so_step4<Word, Entry, PAIR>(D, w.y, k);
+            so_step4<Word, Entry, PAIR>(D, w.z, k);
+            so_step4<Word, Entry, PAIR>(D, w.w, k);
             F[c] = static_cast<uint32_t>(D >> (m - 1)) & 0xFFFFu;
         } else {
             const Word Ds = D;
@@ -191,12 +226,12 @@ __device__ __forceinline__ Word so_local(const uint8_t *seg, Word D, uint32_t tb
                 const uint32_t x = q == 0 ? w.x : q == 1 ? w.y : q == 2 ? w.z : w.w;
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
-                    D = so_update<Word, Entry>(D, so_entry_b<Word, Entry>(x, b, tb, esz), two);
+                    D = so_update<Word, Entry>(D, so_entry_b<Word, Entry>(x, b, k.tb, k.esz), k.two);
                     A |= D;
                 }
             }
             F[c] = ((A >> (m - 1)) & Word(1))
-                       ? so_chunk_flags<Word, Entry>(Ds, seg + 16 * c, tb, m, esz)
+                       ? so_chunk_flags<Word, Entry>(Ds, seg + 16 * c, k.tb, m, k.esz)
                        : 0u;
         }
     }
@@ -206,20 +241,19 @@ __device__ __forceinline__ Word so_local(const uint8_t *seg, Word D, uint32_t tb
 // State at the segment start from the WARM (8 or 16) bytes before it, run
 // from the empty state: exact for every bit below WARM, hence for all bits
 // that matter when m - 1 <= WARM.  Replaces the fix-up for short patterns.
-template <typename Word, typename Entry, int WARM>
-__device__ __forceinline__ Word so_warmup(const uint8_t *seg, uint32_t tb, uint32_t two,
-                                          uint32_t esz) {
+template <typename Word, typename Entry, int WARM, bool PAIR>
+__device__ __forceinline__ Word so_warmup(const uint8_t *seg, const SOK &k) {
     Word D = 0;
     if (WARM == 8) {
         const uint2 w = *reinterpret_cast<const uint2 *>(seg - 8);
-        so_step4<Word, Entry>(D, w.x, tb, two, esz);
-        so_step4<Word, Entry>(D, w.y, tb, two, esz);
+        so_step4<Word, Entry, PAIR>(D, w.x, k);
+        so_step4<Word, Entry, PAIR>(D, w.y, k);
     } else if (WARM == 16) {
         const uint4 w = *reinterpret_cast<const uint4 *>(seg - 16);
-        so_step4<Word, Entry>(D, w.x, tb, two, esz);
-        so_step4<Word, Entry>(D, w.y, tb, two, esz);
-        so_step4<Word, Entry>(D, w.z, tb, two, esz);
-        so_step4<Word, Entry>(D, w.w, tb, two, esz);
+        so_step4<Word, Entry, PAIR>(D, w.x, k);
+        so_step4<Word, Entry, PAIR>(D, w.y, k);
+        so_step4<Word, Entry, PAIR>(D, w.z, k);
+        so_step4<Word, Entry, PAIR>(D, w.w, k);
     }
     return D;
 }
@@ -322,6 +356,8 @@ struct SOItem {
 };
 
 // Loads plan P's mask table into shared memory unless it is there already.
+// Byte tables also get the pair-step table B1[c] = (B[c] << 1) | 1 at
+// tbl + 256.
 template <typename Entry>
 __device__ __forceinline__ void so_table(const PlanDev *P, const PlanDev *&cur_plan, uint8_t *tbl,
                                          uint32_t &m) {
@@ -329,8 +365,19 @@ __device__ __forceinline__ void so_table(const PlanDev *P, const PlanDev *&cur_p
     __syncwarp();  // no lane still reads the old table
     const uint4 *src = reinterpret_cast<const uint4 *>(reinterpret_cast<const uint8_t *>(P) +
                                                        __ldg(&P->off_tbl));
-    for (int c = threadIdx.x & 31; c < static_cast<int>(256 * sizeof(Entry) / 16); c += 32)
-        reinterpret_cast<uint4 *>(tbl)[c] = __ldg(&src[c]);
+    const int lane = threadIdx.x & 31;
+    for (int c = lane; c < static_cast<int>(256 * sizeof(Entry) / 16); c += 32) {
+        const uint4 v = __ldg(&src[c]);
+        reinterpret_cast<uint4 *>(tbl)[c] = v;
+        if (sizeof(Entry) == 1) {
+            // Per byte (b << 1) | 1 within each 32-bit word: shift the word,
+            // drop the bits carried across bytes, set every byte's bit 0.
+            const uint32_t K = 0x01010101u, HI = 0xFEFEFEFEu;
+            reinterpret_cast<uint4 *>(tbl + 256)[c] =
+                make_uint4(((v.x << 1) & HI) | K, ((v.y << 1) & HI) | K, ((v.z << 1) & HI) | K,
+                           ((v.w << 1) & HI) | K);
+        }
+    }
     cur_plan = P;
     m = __ldg(&P->m);
     __syncwarp();
@@ -339,22 +386,20 @@ __device__ __forceinline__ void so_table(const PlanDev *P, const PlanDev *&cur_p
 // Scan of one sub-tile staged at `buf` (its 64 preceding bytes included):
 // flags of the lane's segment, masked to the valid ends.  `carry` is the
 // exact state before the sub-tile (fix-up form only).
-template <typename Word, typename Entry, bool HIST, int WARM>
-__device__ __forceinline__ uint32_t so_subtile(const uint8_t *buf, uint32_t tb, uint32_t m,
-                                               uint32_t two, uint32_t esz, Word &carry,
+template <typename Word, typename Entry, bool HIST, int WARM, bool PAIR>
+__device__ __forceinline__ uint32_t so_subtile(const uint8_t *buf, const SOK &k, uint32_t m, Word &carry,
                                                bool warm_carry, int elo, int ehi,
                                                uint32_t (&F)[SO_SEGC]) {
     const int lane = threadIdx.x & 31;
     const uint8_t *seg = buf + lane * SO_S;
     if (WARM) {
-        so_local<Word, Entry, HIST>(seg, so_warmup<Word, Entry, WARM>(seg, tb, two, esz), tb, m, two,
-                                    esz, F);
+        so_local<Word, Entry, HIST, PAIR>(seg, so_warmup<Word, Entry, WARM, PAIR>(seg, k), k, m, F);
     } else {
-        if (warm_carry && lane == 0) carry = so_warm<Word, Entry>(buf - (m - 1), tb, m, esz);
-        const Word Dend = so_local<Word, Entry, HIST>(seg, Word(0), tb, m, two, esz, F);
+        if (warm_carry && lane == 0) carry = so_warm<Word, Entry>(buf - (m - 1), k.tb, m, k.esz);
+        const Word Dend = so_local<Word, Entry, HIST, false>(seg, Word(0), k, m, F);
         Word Dprev = __shfl_up_sync(0xffffffffu, Dend, 1);
         if (lane == 0) Dprev = carry;
-        so_fixup<Word, Entry>(seg, tb, m, esz, Dprev, F);
+        so_fixup<Word, Entry>(seg, k.tb, m, k.esz, Dprev, F);
         carry = __shfl_sync(0xffffffffu, Dend, 31);
     }
     return so_mask_count(F, elo, ehi);
@@ -414,8 +459,9 @@ __device__ __forceinline__ void so_write_flags(const uint32_t (&F)[SO_SEGC], uin
 template <typename Word, typename Entry, bool HIST, int WARM>
 __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchArgs a) {
     using L = SOLayout<Entry>;
+    constexpr bool PAIR_OK = sizeof(Word) == 4 && sizeof(Entry) == 1 && HIST && WARM != 0;
     extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ __align__(256) uint8_t tbl[256 * sizeof(Entry)];
+    __shared__ __align__(256) uint8_t tbl[256 * sizeof(Entry) + (sizeof(Entry) == 1 ? 256 : 0)];
     const uint32_t tb = smem_addr(tbl);
     uint32_t *hits_base = reinterpret_cast<uint32_t *>(smem + L::HITS_OFF);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L::BAR_OFF);
@@ -430,6 +476,7 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
     if (lane == 0) {
         consts[0] = 2u;
         consts[1] = static_cast<uint32_t>(sizeof(Entry));
+        consts[2] = 4u;
         for (int b = 0; b < SO_NBUF; ++b) mbar_init(&bar[b], 1);
         fence_mbar_init();
         if (so_claim(a, &t, &qi, &k)) {
@@ -446,8 +493,7 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
     t = __shfl_sync(0xffffffffu, t, 0);
     qi = __shfl_sync(0xffffffffu, qi, 0);
     k = __shfl_sync(0xffffffffu, k, 0);
-    const uint32_t two = consts[0];
-    const uint32_t esz = consts[1];
+    const SOK kk{tb, tb + 256u, consts[0], consts[2], consts[1]};
 
     const PlanDev *cur_plan = nullptr;
     uint32_t m = 1;
@@ -558,6 +604,7 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
         // ring slot that no prefetch uses, writing each sub-tile's hits at
         // their final offsets.
         so_table<Entry>(Q.plan, cur_plan, tbl, m);
+        const bool pair = PAIR_OK && m <= 6;
         const uint64_t qn = Q.n;
         const int64_t vlo = o + static_cast<int64_t>(m) - 1;
         const int64_t vhi = o + static_cast<int64_t>(qn);
@@ -576,9 +623,11 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
             const int elo = static_cast<int>(vlo - x > 0 ? vlo - x : int64_t(0));
             const int ehi = static_cast<int>(vhi - x < SO_S ? vhi - x : int64_t(SO_S));
             uint32_t F[SO_SEGC];
+            const uint8_t *buf = smem + wb * SO_BUF + SO_LHALO;
+            const bool first = s == pend.sb && s > 0;
             const uint32_t cnt =
-                so_subtile<Word, Entry, HIST, WARM>(smem + wb * SO_BUF + SO_LHALO, tb, m, two, esz,
-                                                    carry, s == pend.sb && s > 0, elo, ehi, F);
+                pair ? so_subtile<Word, Entry, HIST, WARM, PAIR_OK>(buf, kk, m, carry, first, elo, ehi, F)
+                     : so_subtile<Word, Entry, HIST, WARM, false>(buf, kk, m, carry, first, elo, ehi, F);
             uint32_t total;
             const uint32_t ex = warp_excl_scan(cnt, &total);
             so_write_flags(F, ex, run, cap, out, static_cast<int64_t>(s) * SO_T - shift);
@@ -590,6 +639,7 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
     while (t < a.total) {
         const QueryDev &Q = query_of(a, qi);
         so_table<Entry>(Q.plan, cur_plan, tbl, m);
+        const bool pair = PAIR_OK && m <= 6;  // two bytes per step (see so_step4)
         // Query fields in registers: the mbarrier waits are compiler
         // barriers, after which descriptor fields would be reloaded.
         const uint8_t *const qtext = Q.text;
@@ -633,8 +683,11 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
             const int elo = edge ? static_cast<int>(vlo - x > 0 ? vlo - x : int64_t(0)) : 0;
             const int ehi = edge ? static_cast<int>(vhi - x < SO_S ? vhi - x : int64_t(SO_S)) : SO_S;
             uint32_t F[SO_SEGC];
-            const uint32_t cnt = so_subtile<Word, Entry, HIST, WARM>(
-                smem + cur * SO_BUF + SO_LHALO, tb, m, two, esz, carry, s == sb && s > 0, elo, ehi, F);
+            const uint8_t *buf = smem + cur * SO_BUF + SO_LHALO;
+            const bool first = s == sb && s > 0;
+            const uint32_t cnt =
+                pair ? so_subtile<Word, Entry, HIST, WARM, PAIR_OK>(buf, kk, m, carry, first, elo, ehi, F)
+                     : so_subtile<Word, Entry, HIST, WARM, false>(buf, kk, m, carry, first, elo, ehi, F);
             uint32_t total = 0, ex = 0;
             if (__any_sync(0xffffffffu, cnt != 0)) ex = warp_excl_scan(cnt, &total);
             if (total != 0 && spill) {

@@ -46,10 +46,14 @@ constexpr int SO_S = SO_SEGC * 16;          // 144 bytes per lane (>= m for m <=
 constexpr uint32_t SO_T = 32 * SO_S;        // end positions per sub-tile (one warp)
 constexpr uint32_t SO_LHALO = 64;           // bytes staged before the sub-tile (>= m-1)
 constexpr uint32_t SO_BUF = SO_LHALO + SO_T;
+// Staging ring: SO_NBUF - 1 sub-tiles in flight while one is scanned.  Two
+// slots (9.3 KB a block) leave room for ~21 resident one-warp blocks per
+// SM, whose scans hide the copy latency and each other's dependent steps;
+// three slots (14 KB) allowed only 15 and scanned 8-16 % fewer bytes/s.
 #ifndef SO_NBUF_SLOTS
-#define SO_NBUF_SLOTS 3
+#define SO_NBUF_SLOTS 2
 #endif
-constexpr int SO_NBUF = SO_NBUF_SLOTS;      // staging ring: SO_NBUF-1 sub-tiles in flight while one is scanned
+constexpr int SO_NBUF = SO_NBUF_SLOTS;
 // Hits of one work item kept in shared memory (two buffers).  Zero: every
 // hit goes to the spill area (L2-resident), which leaves the shared memory
 // to the staging ring and lets 15 one-warp blocks share an SM.

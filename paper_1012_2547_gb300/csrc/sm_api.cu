@@ -321,11 +321,13 @@ sm_status build_blob(const uint8_t *p, uint32_t m, uint32_t sigma, const sm_conf
         const uint32_t s = m - q + 1;
         // Base range per thread ~4 KiB of start positions; a launch may give
         // a thread several base ranges (sub_per_item).
-        // Probes per thread range: about 4 KiB of starts, at least 32 (a
-        // warp's 32 lanes then take at least 32 rounds of probes per work
-        // unit) and at most 256; fewer only where 128 ranges would pass 2^32
-        // starts.
-        uint32_t ppt = src->tile ? (1u << std::min(src->tile, 20u)) / s : std::max(32u, 4096u / s);
+        // Probes per thread range: about 1 KiB of starts (2 to 256 probes;
+        // fewer only where 128 ranges would pass 2^32 starts).  Short units
+        // keep many blocks busy on a short text, including when an item falls
+        // back to the linear scan (one thread per range); a launch over a
+        // long text gives each work item many units (sub_per_item), so the
+        // filter still runs many probe rounds per item there.
+        uint32_t ppt = src->tile ? (1u << std::min(src->tile, 20u)) / s : 1024u / s;
         ppt = std::max(2u, std::min(ppt, 256u));
         while (ppt > 2 && static_cast<uint64_t>(ppt) * s * qg_kernel_threads() >= (1ull << 32)) ppt /= 2;
         R = static_cast<uint64_t>(ppt) * s;

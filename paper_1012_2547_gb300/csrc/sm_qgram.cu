@@ -349,7 +349,6 @@ __device__ bool qgram_warp(const PlanView &v, uint64_t patw, const uint8_t *text
     const uint64_t k0 = Lw / s;
     const uint64_t kend = min(k0 + span / s, (n - v.m) / s + 1);  // probes [k0, kend) hold valid starts
     const uint64_t nr = kend > k0 ? (kend - k0 + 31) / 32 : 0;
-    const uint64_t budget = static_cast<uint64_t>(QG_ROUNDS_PER_PROBE) * 32u * nr + 32u;
     const uint64_t qmask = v.q >= 8 ? ~0ull : ((1ull << (8u * v.q)) - 1ull);
     run = QGRun{0, 0, 0};
     for (uint64_t r0 = 0; r0 < nr; r0 += QG_U) {
@@ -391,6 +390,10 @@ __device__ bool qgram_warp(const PlanView &v, uint64_t patw, const uint8_t *text
             const bool hit = (hits >> u) & 1u;
             if (!__any_sync(0xffffffffu, hit)) continue;
             const uint64_t kp = k0 + (r0 + u) * 32u + lane;
+            // Density guard, checked as the rounds go: at most
+            // QG_ROUNDS_PER_PROBE full checks per probe so far (plus slack),
+            // so a dense item is given up within a round or two.
+            const uint64_t budget = static_cast<uint64_t>(QG_ROUNDS_PER_PROBE) * 32u * (r0 + u + 1) + 64u;
             if (!qgram_round(v, patw, text, n, Lw, hit, kp * s + s - 1u, budget, o, run)) return false;
         }
     }

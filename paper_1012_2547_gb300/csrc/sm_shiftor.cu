@@ -9,7 +9,7 @@
 // and an occurrence ends at e iff bit m-1 of D is 1 (it starts at e-m+1).
 //
 // GB300 mapping
-//   * One warp per block; ~16 blocks per SM.  A warp claims work items
+//   * One warp per block; ~21 blocks per SM.  A warp claims work items
 //     (query, item) from a device counter; an item is `sub_per_item`
 //     consecutive sub-tiles of 32 * 144 end positions whose bytes (plus the
 //     64 bytes before them) are staged HBM -> shared memory by one

@@ -32,8 +32,10 @@ VARIANT_IDS = {"shiftor": 1, "qgram": 2, "linear": 3, "dfa": 4}
 DFA_MAX_TABLE = 32768 - 256  # the library's bound on an automaton's table (bytes)
 # Work-item sizes tried for the fastest family (log2 bytes; 0 = the
 # library's default): Shift-Or: shortest work item; q-gram and automaton:
-# start positions per thread range.
-TILES = {"shiftor": (0, 17, 19), "qgram": (0, 11, 14, 16), "dfa": (0, 12), "linear": (0,)}
+# start positions per thread range.  q-gram ranges stay at most 4 KiB: an
+# item that falls back to the linear scan runs one thread per range, so
+# long ranges would leave a dense short text to a few blocks.
+TILES = {"shiftor": (0, 17, 19), "qgram": (0, 9, 11, 12), "dfa": (0, 12), "linear": (0,)}
 
 
 def m_bucket(m: int) -> int:

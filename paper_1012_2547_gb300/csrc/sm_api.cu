@@ -11,8 +11,11 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <condition_variable>
+#include <functional>
 #include <cstdlib>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -506,6 +509,75 @@ sm_status build_blob(const uint8_t *p, uint32_t m, uint32_t sigma, const sm_conf
     return SM_OK;
 }
 
+// Host worker threads for plan building, started on first use and kept:
+// starting threads on every call cost more than building a thousand plans.
+// run(n, fn) calls fn(0..n-1) on the workers and the calling thread and
+// returns when all calls have returned; concurrent run()s take turns.
+class HostPool {
+  public:
+    static HostPool &get() {
+        static HostPool *P = new HostPool();  // never destroyed: workers may be idle at exit
+        return *P;
+    }
+    unsigned threads() const { return static_cast<unsigned>(workers_.size()) + 1; }
+    void run(unsigned n, const std::function<void(unsigned)> &fn) {
+        std::lock_guard<std::mutex> one(run_mu_);
+        {
+            std::lock_guard<std::mutex> g(mu_);
+            job_ = &fn;
+            njob_ = n;
+            next_ = 0;
+            remaining_ = n;
+            ++gen_;
+        }
+        cv_.notify_all();
+        work();
+        std::unique_lock<std::mutex> g(mu_);
+        done_cv_.wait(g, [&] { return remaining_ == 0; });
+        job_ = nullptr;
+    }
+
+  private:
+    HostPool() {
+        const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+        const unsigned n = std::min(hw, 32u) - 1;
+        for (unsigned i = 0; i < n; ++i) workers_.emplace_back([this] { loop(); });
+    }
+    // Takes tasks of the current job until none is left.
+    void work() {
+        while (true) {
+            unsigned t;
+            const std::function<void(unsigned)> *fn;
+            {
+                std::lock_guard<std::mutex> g(mu_);
+                if (!job_ || next_ >= njob_) return;
+                t = next_++;
+                fn = job_;
+            }
+            (*fn)(t);
+            std::lock_guard<std::mutex> g(mu_);
+            if (--remaining_ == 0) done_cv_.notify_all();
+        }
+    }
+    void loop() {
+        uint64_t seen = 0;
+        while (true) {
+            {
+                std::unique_lock<std::mutex> g(mu_);
+                cv_.wait(g, [&] { return gen_ != seen; });
+                seen = gen_;
+            }
+            work();
+        }
+    }
+    std::mutex run_mu_, mu_;
+    std::condition_variable cv_, done_cv_;
+    std::vector<std::thread> workers_;
+    const std::function<void(unsigned)> *job_ = nullptr;
+    unsigned njob_ = 0, next_ = 0, remaining_ = 0;
+    uint64_t gen_ = 0;
+};
+
 // Pinned host staging for plan uploads, reused across calls: a copy from
 // pageable memory goes through a driver bounce buffer at a fraction of the
 // link's rate.  Its mutex is held from the fill to the stream sync that
@@ -538,19 +610,14 @@ sm_status prepare_many(const uint8_t *patterns, const uint32_t *lengths, uint32_
         pat_off[i] = pos;
         pos += lengths[i];
     }
-    // Host tables of many patterns are built on several threads.
+    // Host tables of many patterns are built on the pool's threads (small
+    // calls on the caller's thread alone).
     std::vector<sm_status> sts(count, SM_OK);
-    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-    const unsigned nth = static_cast<unsigned>(std::min<uint64_t>(std::min(hw, 16u), (pos >> 14) + 1));
-    auto on_threads = [&](auto &&fn) {
-        if (nth <= 1 || count < 64) {
-            for (unsigned t = 0; t < nth; ++t) fn(t);
-        } else {
-            std::vector<std::thread> pool;
-            for (unsigned t = 1; t < nth; ++t) pool.emplace_back(fn, t);
-            fn(0);
-            for (auto &th : pool) th.join();
-        }
+    const bool many = count >= 64;
+    const unsigned nth = many ? HostPool::get().threads() : 1u;
+    auto on_threads = [&](const std::function<void(unsigned)> &fn) {
+        if (!many) fn(0);
+        else HostPool::get().run(nth, fn);
     };
     on_threads([&](unsigned t) {
         for (uint32_t i = t; i < count; i += nth)
@@ -1036,16 +1103,88 @@ sm_status batch_layout(const sm_query *qs, uint32_t nq, uint8_t *base, sm_batch 
 
 // Copies a laid-out batch's descriptors, zero list and packs to `base`
 // (pageable sources: each copy returns once its bytes are staged).
+// Pinned host ring for batch uploads that must not block the host: a span
+// is filled on the host, copied by cudaMemcpyAsync on the caller's stream,
+// and reused only once an event recorded behind that copy has completed.
+// (A copy from pageable memory may wait for the work already queued on the
+// stream, which would keep the host from preparing the next batch while the
+// GPU runs this one.)  Spans are handed out in ring order; a request that
+// does not fit waits for the oldest spans it overlaps.  Larger requests than
+// a quarter of the ring, or a ring that could not be allocated, use a plain
+// copy.
+class UploadRing {
+  public:
+    static UploadRing &get() {
+        static UploadRing *R = new UploadRing();  // never destroyed: copies may be in flight at exit
+        return *R;
+    }
+    cudaError_t copy(void *dst, const void *src, size_t bytes, cudaStream_t stream) {
+        if (bytes == 0) return cudaSuccess;
+        std::lock_guard<std::mutex> g(mu_);
+        const size_t need = (bytes + 255) & ~size_t(255);
+        if (!buf_ && !tried_) {
+            tried_ = true;
+            if (cudaHostAlloc(reinterpret_cast<void **>(&buf_), kCap, cudaHostAllocDefault) != cudaSuccess) {
+                buf_ = nullptr;
+                (void)cudaGetLastError();
+            }
+        }
+        if (!buf_ || need > kCap / 4) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, stream);
+        while (!live_.empty() && cudaEventQuery(live_.front().ev) == cudaSuccess) {
+            cudaEventDestroy(live_.front().ev);
+            live_.pop_front();
+        }
+        (void)cudaGetLastError();  // cudaErrorNotReady from the query is not an error
+        const size_t at = head_ + need <= kCap ? head_ : 0;
+        // While any span in flight overlaps [at, at + need), wait for the
+        // oldest one and drop it (older spans are waited for first).
+        auto overlapped = [&] {
+            for (const Span &o : live_)
+                if (o.off < at + need && at < o.off + o.bytes) return true;
+            return false;
+        };
+        while (overlapped()) {
+            const Span &o = live_.front();
+            cudaError_t e = cudaEventSynchronize(o.ev);
+            cudaEventDestroy(o.ev);
+            live_.pop_front();
+            if (e != cudaSuccess) return e;
+        }
+        std::memcpy(buf_ + at, src, bytes);
+        cudaError_t e = cudaMemcpyAsync(dst, buf_ + at, bytes, cudaMemcpyHostToDevice, stream);
+        if (e != cudaSuccess) return e;
+        cudaEvent_t ev;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ev, stream);
+        if (e != cudaSuccess) {
+            cudaStreamSynchronize(stream);  // the span is free once the copy is done
+            return e;
+        }
+        live_.push_back(Span{at, need, ev});
+        head_ = at + need;
+        return cudaSuccess;
+    }
+
+  private:
+    static constexpr size_t kCap = size_t(64) << 20;
+    struct Span {
+        size_t off, bytes;
+        cudaEvent_t ev;
+    };
+    std::mutex mu_;
+    uint8_t *buf_ = nullptr;
+    bool tried_ = false;
+    size_t head_ = 0;
+    std::deque<Span> live_;  // copies in flight, oldest first
+};
+
 sm_status batch_upload(const BatchLayout &L, uint8_t *base, cudaStream_t stream) {
+    UploadRing &R = UploadRing::get();
     if (!L.desc.empty())
-        SM_TRY_CUDA(cudaMemcpyAsync(base + L.desc_off, L.desc.data(), L.desc.size() * sizeof(QueryDev),
-                                    cudaMemcpyHostToDevice, stream));
+        SM_TRY_CUDA(R.copy(base + L.desc_off, L.desc.data(), L.desc.size() * sizeof(QueryDev), stream));
     if (!L.zero.empty())
-        SM_TRY_CUDA(cudaMemcpyAsync(base + L.zero_off, L.zero.data(), L.zero.size() * sizeof(uint64_t *),
-                                    cudaMemcpyHostToDevice, stream));
-    if (!L.packs.empty())
-        SM_TRY_CUDA(cudaMemcpyAsync(base + L.pack_off, L.packs.data(), L.packs.size(),
-                                    cudaMemcpyHostToDevice, stream));
+        SM_TRY_CUDA(R.copy(base + L.zero_off, L.zero.data(), L.zero.size() * sizeof(uint64_t *), stream));
+    if (!L.packs.empty()) SM_TRY_CUDA(R.copy(base + L.pack_off, L.packs.data(), L.packs.size(), stream));
     return SM_OK;
 }
 

@@ -994,9 +994,10 @@ def serve_record(args, local, loads=None) -> dict:
     for frac in (args.serve_loads if loads is None else loads):
         st, _ = run_server(arrival_rate=frac * sat["qps"])
         by_load[str(frac)] = {"offered_qps": round(frac * sat["qps"], 1), "qps": st["qps"],
+                            "served_over_offered": round(st["qps"] / (frac * sat["qps"]), 3),
                             "p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
-                            "batches": st["batches"], "host_s": st["host_s"],
-                            "pinned_pool_bytes": st["pinned_pool_bytes"]}
+                            "by_length_class": st["by_length_class"], "batches": st["batches"],
+                            "retries": st["retries"], "rates": st["rates"], "host_s": st["host_s"]}
     out = {
         "workload": f"serve_{len(reqs)}q_corpus{C}", "metric": "served queries/s, p50/p99 latency",
         "queries": len(reqs), "scanned_bytes": scanned,
@@ -1116,7 +1117,7 @@ def main():
             # compact form, so one default run reports every half of the
             # metric (each also runs alone: --workload bandwidth / serve).
             out["bandwidth"] = bandwidth_record(args, local, compact=True)
-            out["serve"] = serve_record(args, local, loads=[0.5, 0.8])
+            out["serve"] = serve_record(args, local, loads=[0.5, 0.8, 0.95])
         if rank == 0:
             print(json.dumps(out), flush=True)
     finally:

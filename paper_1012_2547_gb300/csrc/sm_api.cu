@@ -866,7 +866,48 @@ struct BatchLayout {
     std::vector<QueryDev> desc;
     std::vector<uint64_t *> zero;
     std::vector<uint8_t> packs;  // PackPlan blocks, MP_PLAN_BYTES each
+    size_t tmap_off = 0;
+    std::vector<uint64_t> tmap;  // ticket maps of the groups that have one, back to back
 };
+
+// Texts at least this long are worth reading once for all the queries of
+// a launch that scan them (their items interleaved by text position);
+// shorter texts stay in L2 across queries anyway.
+constexpr uint64_t kShareTextBytes = uint64_t(32) << 20;
+
+// Ticket map of one launch group (LaunchArgs::tmap): appends its entries to
+// `out` and returns true, or returns false (plain query-by-query tickets)
+// when no long text is shared by two of its queries.  Entry order: by text,
+// then by the byte offset where the item starts in the text, then by query;
+// each query's items stay in increasing order.  items[i], unit_bytes[i] and
+// per[i]: work items, bytes per unit and units per item of the group's
+// i-th query.
+bool ticket_map(const std::vector<const uint8_t *> &text, const std::vector<uint64_t> &n,
+                const std::vector<uint64_t> &items, const std::vector<uint64_t> &unit_bytes,
+                const std::vector<uint32_t> &per, std::vector<uint64_t> *out) {
+    std::map<std::pair<const uint8_t *, uint64_t>, uint32_t> users;
+    bool shared = false;
+    for (size_t i = 0; i < text.size(); ++i)
+        if (n[i] >= kShareTextBytes && ++users[{text[i], n[i]}] >= 2) shared = true;
+    if (!shared || text.size() >= (1u << 24)) return false;
+    struct E {
+        const uint8_t *t;
+        uint64_t start;
+        uint32_t q;
+        uint64_t item;
+    };
+    std::vector<E> es;
+    for (size_t i = 0; i < text.size(); ++i)
+        for (uint64_t k = 0; k < items[i]; ++k)
+            es.push_back(E{text[i], k * per[i] * unit_bytes[i], static_cast<uint32_t>(i), k});
+    std::stable_sort(es.begin(), es.end(), [](const E &a, const E &b) {
+        if (a.t != b.t) return a.t < b.t;
+        if (a.start != b.start) return a.start < b.start;
+        return a.q < b.q;
+    });
+    for (const E &e : es) out->push_back((static_cast<uint64_t>(e.q) << 40) | e.item);
+    return true;
+}
 
 // A pattern can join a multi-pattern pack: Shift-And with a 1- or 2-byte
 // mask table (m <= 16) and an alphabet-size hint with sigma^m >= 2^16, so
@@ -992,12 +1033,41 @@ sm_status batch_layout(const sm_query *qs, uint32_t nq, uint8_t *base, sm_batch 
             for (uint32_t i : by_kid[k]) t += ntiles[i];
         if (t) spill_need = std::max(spill_need, static_cast<size_t>(grid_for(k, t)) * so_spill_bytes());
     }
-    const size_t spill_off = (L->pack_off + packs.size() * MP_PLAN_BYTES + 255) & ~size_t(255);
+    // Ticket maps (sizes first: entries are filled below, group by group).
+    std::vector<std::vector<uint64_t>> maps;
+    L->tmap.clear();
+    {
+        auto map_of = [&](const std::vector<uint32_t> &qidx, int k, bool is_pack) {
+            std::vector<const uint8_t *> t;
+            std::vector<uint64_t> nn, it, ub;
+            std::vector<uint32_t> pr;
+            for (size_t j = 0; j < qidx.size(); ++j) {
+                const uint32_t i = is_pack ? packs[qidx[j]][0] : qidx[j];
+                t.push_back(qs[i].text);
+                nn.push_back(qs[i].n);
+                it.push_back(is_pack ? ntiles_pack[qidx[j]] : ntiles[i]);
+                ub.push_back(is_pack ? so_tile_starts() : kernel_tile_starts(k, qs[i].plan->hdr));
+                pr.push_back(is_pack ? per_pack[qidx[j]] : per_q[i]);
+            }
+            std::vector<uint64_t> m;
+            if (!ticket_map(t, nn, it, ub, pr, &m)) m.clear();
+            return m;
+        };
+        for (int k = 0; k < K_COUNT; ++k) maps.push_back(by_kid[k].empty() ? std::vector<uint64_t>() : map_of(by_kid[k], k, false));
+        std::vector<uint32_t> pk(packs.size());
+        for (size_t j = 0; j < packs.size(); ++j) pk[j] = static_cast<uint32_t>(j);
+        maps.push_back(packs.empty() ? std::vector<uint64_t>() : map_of(pk, K_SOMULTI, true));
+    }
+    size_t tmap_entries = 0;
+    for (const auto &m : maps) tmap_entries += m.size();
+    L->tmap_off = (L->pack_off + packs.size() * MP_PLAN_BYTES + 255) & ~size_t(255);
+    const size_t spill_off = (L->tmap_off + tmap_entries * sizeof(uint64_t) + 255) & ~size_t(255);
     L->bytes = spill_off + spill_need + 16;
     L->desc.reserve(ndesc);
     uint64_t state_pos = 0;
     int gi = 0;
-    auto add_group = [&](int k, size_t first_desc, uint32_t count, uint64_t tickets) -> sm_status {
+    auto add_group = [&](int k, size_t first_desc, uint32_t count, uint64_t tickets,
+                         const std::vector<uint64_t> &map) -> sm_status {
         if (gi >= static_cast<int>(kTicketBytes / 8)) return SM_EINVAL;
         sm_batch::Group g{};
         g.kid = k;
@@ -1008,6 +1078,10 @@ sm_status batch_layout(const sm_query *qs, uint32_t nq, uint8_t *base, sm_batch 
         g.args.total = tickets;
         g.args.err = lib().err;
         g.args.spill = staged_kid(k) ? base + spill_off : nullptr;
+        if (!map.empty()) {
+            g.args.tmap = reinterpret_cast<const uint64_t *>(base + L->tmap_off) + L->tmap.size();
+            L->tmap.insert(L->tmap.end(), map.begin(), map.end());
+        }
         g.grid = grid_for(k, tickets);
         b->groups.push_back(g);
         ++gi;
@@ -1034,7 +1108,7 @@ sm_status batch_layout(const sm_query *qs, uint32_t nq, uint8_t *base, sm_batch 
             state_pos += ntiles[i];
             L->desc.push_back(d);
         }
-        st = add_group(k, first_desc, static_cast<uint32_t>(by_kid[k].size()), ticket);
+        st = add_group(k, first_desc, static_cast<uint32_t>(by_kid[k].size()), ticket, maps[k]);
         if (st != SM_OK) return st;
     }
     if (!packs.empty()) {
@@ -1090,7 +1164,7 @@ sm_status batch_layout(const sm_query *qs, uint32_t nq, uint8_t *base, sm_batch 
             }
         }
         L->desc.insert(L->desc.end(), members.begin(), members.end());
-        st = add_group(K_SOMULTI, first_head, static_cast<uint32_t>(packs.size()), ticket);
+        st = add_group(K_SOMULTI, first_head, static_cast<uint32_t>(packs.size()), ticket, maps[K_COUNT]);
         if (st != SM_OK) return st;
     }
     b->base = base;
@@ -1185,6 +1259,8 @@ sm_status batch_upload(const BatchLayout &L, uint8_t *base, cudaStream_t stream)
     if (!L.zero.empty())
         SM_TRY_CUDA(R.copy(base + L.zero_off, L.zero.data(), L.zero.size() * sizeof(uint64_t *), stream));
     if (!L.packs.empty()) SM_TRY_CUDA(R.copy(base + L.pack_off, L.packs.data(), L.packs.size(), stream));
+    if (!L.tmap.empty())
+        SM_TRY_CUDA(R.copy(base + L.tmap_off, L.tmap.data(), L.tmap.size() * sizeof(uint64_t), stream));
     return SM_OK;
 }
 

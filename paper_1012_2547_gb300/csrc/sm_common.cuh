@@ -82,7 +82,16 @@ struct LaunchArgs {
     unsigned long long total;    // total tickets
     uint32_t *err;               // device error word (bit flags)
     uint8_t *spill;              // bit-parallel kernel: per-block flag spill area, or null
+    // Ticket map, or null.  Entry t is (query index << 40) | item: the
+    // launch's items in the order the host chose (items of queries that
+    // share a text interleaved by text position, so the text streams
+    // through L2 once for all of them).  Each query's items still come in
+    // increasing order, which the look-back needs.  Null: tickets run
+    // query by query, [first_ticket, first_ticket + ntiles) per query.
+    const uint64_t *tmap;
 };
+
+constexpr uint64_t TMAP_ITEM_MASK = (1ull << 40) - 1;
 
 enum : uint32_t { ERR_TIMEOUT = 1u, ERR_COPY = 2u };
 
@@ -308,6 +317,12 @@ __device__ __forceinline__ uint64_t lookback_exclusive(uint64_t *state, uint64_t
 // Ticket -> (query index, tile) for a launch.
 __device__ __forceinline__ void resolve_ticket(const LaunchArgs &a, unsigned long long t,
                                                uint32_t *qi, uint64_t *tile) {
+    if (a.tmap) {
+        const uint64_t e = __ldg(&a.tmap[t]);
+        *qi = static_cast<uint32_t>(e >> 40);
+        *tile = e & TMAP_ITEM_MASK;
+        return;
+    }
     if (a.nq == 1) {
         *qi = 0;
         *tile = t;

@@ -4,30 +4,35 @@ Requests arrive at any time (``Server.submit``); each names a resident
 corpus (a device text loaded once) or carries its own text.  A scheduler
 thread repeatedly
 
-  1. retires finished batches (their stream's event has fired): reads the
-     counts and positions copied back on that stream, completes the
-     requests' futures, re-queues any request whose output was truncated
-     with its exact count as the new capacity, and returns its memory to
-     the budget;
+  1. retires finished work: when a batch's counts are on the host, requests
+     whose output was truncated go back to the front of the queue with
+     their exact count as the new capacity, and the valid positions of the
+     others are copied back; each request completes (its future gets its
+     positions) as soon as its own copy is done, and the batch's memory
+     returns to the budget when all of it is;
   2. admits pending requests while their device memory (own text, plan,
      output capacity, count) plus the batch workspace fits the budget,
      taking requests of one length class (floor(log2 m): the class of the
      oldest pending request) in arrival order, up to ``max_batch`` requests
-     and ``max_batch_scan_bytes`` of text to scan (which bounds the GPU
-     time of a batch, and so the wait of the requests behind it);
+     and an estimated GPU time of ``max_batch_seconds`` (scan bytes and
+     output bytes over rates measured on the batches already run), which
+     bounds how long the requests behind a batch wait; the bound grows with
+     the backlog, so a long queue drains in large batches;
   3. launches the batch on a free stream with ``sm_search_batch_async``
      (one persistent launch per kernel family, in memory the server owns),
-     followed by the copy of the counts and an event; once the counts are
-     on the host, exactly the valid positions of each request are copied
-     back (a second event): small results through a per-stream pinned
-     staging buffer, large ones straight into a pinned block of their own
-     that the client receives without a copy (``PinnedPool``).
+     followed by the copy of the counts and an event; small results come
+     back through a per-stream pinned staging buffer, large ones straight
+     into a pinned block of their own that the client receives without a
+     copy (``PinnedPool``).
 
-Up to ``streams`` batches are in flight at once, so requests that arrive
-while others run are admitted as slots and memory free up and their work
-overlaps on the device.  Every request records arrival and completion times
-(p50 / p99 latency).  ``Policy`` holds the host-side decisions (admission,
-length classes, batch size) and needs no GPU.
+A first attempt's output capacity is sized from the count expected for the
+pattern's bytes under the text's byte frequencies, so few requests need a
+second attempt.  Up to ``streams`` batches are in flight at once, so
+requests that arrive while others run are admitted as slots and memory
+free up and their work overlaps on the device.  Every request records
+arrival and completion times (p50 / p99 latency, also per length class).
+``Policy`` holds the host-side decisions (admission, length classes, batch
+size) and needs no GPU.
 """
 from __future__ import annotations
 
@@ -77,15 +82,21 @@ class Policy:
     def __init__(self, budget_bytes: int, max_batch: int = 512, max_wait: float = 0.0005,
                  corpus_bytes=None, workspace_per_batch: int = 128 << 20,
                  max_batch_out_bytes: int = 1 << 62, max_batch_scan_bytes: int = 1 << 62,
-                 scan_backlog: int = 512):
+                 scan_backlog: int = 512, max_batch_seconds: float = 1e9,
+                 scan_rate: float = 3e12, copy_rate: float = 1.5e11):
         self.budget = int(budget_bytes)
         self.max_batch_out = int(max_batch_out_bytes)
-        # Text bytes one batch may scan: bounds a batch's GPU time, so a
-        # request never waits behind hundreds of long scans.  The bound
-        # grows by one step per `scan_backlog` pending requests: a backlog
-        # is drained in large batches (throughput), a short queue in small
-        # ones (latency).
+        # Bounds of one batch's GPU time, so a request never waits behind
+        # hundreds of long scans or copies: a hard bound on the text bytes it
+        # scans, and a bound on its estimated time (scan_bytes / scan_rate +
+        # output bytes / copy_rate, the rates measured on the batches that
+        # ran: observe()).  Both grow by one step per `scan_backlog` pending
+        # requests: a backlog is drained in large batches (throughput), a
+        # short queue in small ones (latency).
         self.max_batch_scan = int(max_batch_scan_bytes)
+        self.max_batch_seconds = float(max_batch_seconds)
+        self.scan_rate = float(scan_rate)
+        self.copy_rate = float(copy_rate)
         self.scan_backlog = max(1, int(scan_backlog))
         self.max_batch = int(max_batch)
         self.max_wait = float(max_wait)
@@ -100,6 +111,21 @@ class Policy:
 
     def scan_bytes(self, r: Request) -> int:
         return len(r.text) if r.text is not None else int(self.corpus_bytes.get(r.corpus, 0))
+
+    def cost(self, r: Request) -> float:
+        """Estimated GPU seconds of a request: its scan and its copy-back."""
+        return self.scan_bytes(r) / self.scan_rate + 8 * max(r.cap, 1) / self.copy_rate
+
+    def observe(self, scan_bytes: int, scan_s: float, out_bytes: int, copy_s: float) -> None:
+        """Measured timings of a finished batch update the rate estimates
+        (exponential moving averages, each sample bounded to a factor of 4
+        of the current estimate)."""
+        if scan_s > 0 and scan_bytes > (64 << 20):
+            r = min(max(scan_bytes / scan_s, self.scan_rate / 4), self.scan_rate * 4)
+            self.scan_rate = 0.8 * self.scan_rate + 0.2 * r
+        if copy_s > 0 and out_bytes > (8 << 20):
+            r = min(max(out_bytes / copy_s, self.copy_rate / 4), self.copy_rate * 4)
+            self.copy_rate = 0.8 * self.copy_rate + 0.2 * r
 
     def push(self, r: Request, front: bool = False) -> None:
         (self.pending.appendleft if front else self.pending.append)(r)
@@ -126,17 +152,21 @@ class Policy:
             return [], 0, rejected
         keep = collections.deque()
         out_bytes = scan = 0
-        scan_cap = self.max_batch_scan * (1 + len(self.pending) // self.scan_backlog)
+        secs = 0.0
+        steps = 1 + len(self.pending) // self.scan_backlog
+        scan_cap = self.max_batch_scan * steps
+        time_cap = self.max_batch_seconds * steps
         while self.pending and len(batch) < self.max_batch:
             r = self.pending.popleft()
             need = self.need(r)
             fits_out = not batch or out_bytes + 8 * r.cap <= self.max_batch_out
-            fits_scan = not batch or scan + self.scan_bytes(r) <= scan_cap
+            fits_scan = not batch or (scan + self.scan_bytes(r) <= scan_cap and secs + self.cost(r) <= time_cap)
             if length_class(r.m) == cls and self.used + reserved + need <= self.budget and fits_out and fits_scan:
                 batch.append(r)
                 reserved += need
                 out_bytes += 8 * r.cap
                 scan += self.scan_bytes(r)
+                secs += self.cost(r)
             else:
                 keep.append(r)
                 if self.used + reserved + need > self.budget and length_class(r.m) == cls:
@@ -230,7 +260,8 @@ class Server:
                  max_batch: int = 512, max_wait: float = 0.0005, first_cap: int = 256,
                  sigma_hints: dict | None = None, own_text_sigma: int = 0,
                  staging_bytes: int = 256 << 20, pinned_pool_bytes: int | None = None,
-                 max_batch_scan_bytes: int = 16 << 30):
+                 max_batch_scan_bytes: int = 64 << 30, max_batch_seconds: float = 0.008,
+                 cap_factor: float = 2.0):
         import torch
 
         import paper_1012_2547_gb300 as smg
@@ -246,9 +277,19 @@ class Server:
                 self.sigma_hints[name] = effective_sigma(t[: 1 << 20].cpu().numpy())
         self.own_text_sigma = own_text_sigma
         self.first_cap = int(first_cap)
+        self.cap_factor = float(cap_factor)
+        # Byte frequencies of each corpus (a histogram of its first 16 MiB,
+        # on the device): a first attempt's capacity is sized from the count
+        # expected for the pattern's own bytes.
+        self.freqs = {}
+        for name, t in self.corpora.items():
+            h = torch.bincount(t[: 16 << 20].to(torch.int32), minlength=256).double()
+            self.freqs[name] = (h / max(float(h.sum()), 1.0)).cpu().numpy()
         self.policy = Policy(budget_bytes, max_batch, max_wait,
                              {k: v.numel() for k, v in self.corpora.items()},
-                             max_batch_scan_bytes=max_batch_scan_bytes)
+                             max_batch_scan_bytes=max_batch_scan_bytes,
+                             max_batch_seconds=max_batch_seconds)
+        self.lat_by_class = collections.defaultdict(list)
         self.streams = [torch.cuda.Stream() for _ in range(streams)]
         self.inflight: list[dict | None] = [None] * streams
         # Per-stream pinned staging for the copy-back of small results
@@ -291,23 +332,28 @@ class Server:
                                                           if isinstance(text, (bytes, bytearray))
                                                           else text, dtype=np.uint8)
         n = len(t) if t is not None else self.corpora[corpus].numel()
-        r = Request(next(self._ids), p, corpus, t, self._first_cap(n, len(p), corpus),
+        r = Request(next(self._ids), p, corpus, t, self._first_cap(n, p, corpus, t),
                     time.perf_counter() if t_arrival is None else t_arrival)
         with self._lock:
             self.policy.push(r)
         self._wake.set()
         return r.future
 
-    def _first_cap(self, n: int, m: int, corpus: str | None) -> int:
-        """Output capacity of a first attempt: for a corpus with an alphabet
-        hint, twice the count expected on a uniform text, (n-m+1)/sigma^m,
-        plus first_cap; else first_cap.  A larger true count costs a retry."""
+    def _first_cap(self, n: int, p: bytes, corpus: str | None, text) -> int:
+        """Output capacity of a first attempt: first_cap plus cap_factor
+        times the count expected if the text's bytes were independent with
+        its byte frequencies, (n-m+1) * prod_j f(p[j]) (the corpus's
+        histogram, or that of the first 64 KiB of an own text).  A larger true
+        count costs a retry."""
+        m = len(p)
         starts = max(n - m + 1, 1)
-        sigma = self.sigma_hints.get(corpus, 0) if corpus is not None else self.own_text_sigma
-        cap = self.first_cap
-        if sigma >= 2 and m * np.log2(sigma) < 62:
-            cap += int(2 * starts / float(sigma) ** m)
-        return min(cap, starts)
+        if corpus is not None:
+            f = self.freqs[corpus]
+        else:
+            sample = text[: 1 << 16]
+            f = np.bincount(sample, minlength=256) / max(len(sample), 1)
+        pr = float(np.prod(f[np.frombuffer(p, np.uint8)]))
+        return int(min(self.first_cap + np.ceil(self.cap_factor * starts * pr), starts))
 
     def close(self, timeout: float | None = None) -> None:
         self._stop = True
@@ -318,9 +364,17 @@ class Server:
 
     def stats(self) -> dict:
         lat = np.array(self.latencies) if self.latencies else np.zeros(1)
+        by_class = {}
+        for c, v in sorted(self.lat_by_class.items()):
+            a = np.array(v)
+            by_class[f"m{1 << c}-{(2 << c) - 1}"] = {"n": len(v), "p50_ms": round(float(np.percentile(a, 50)) * 1e3, 3),
+                                                  "p99_ms": round(float(np.percentile(a, 99)) * 1e3, 3)}
         return {"completed": self.completed, "batches": self.batches, "retries": self.retries,
                 "pinned_pool_bytes": self.pool.allocated_bytes,
                 "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "by_length_class": by_class,
+                "rates": {"scan_GBs": round(self.policy.scan_rate / 1e9, 1),
+                          "copy_GBs": round(self.policy.copy_rate / 1e9, 1)},
                 "host_s": {k: round(v, 4) for k, v in self.host_s.items()}}
 
     # ---------------------------------------------------------------- loop
@@ -363,6 +417,8 @@ class Server:
         dev = torch.device("cuda")
         t0 = time.perf_counter()
         with torch.cuda.stream(s):
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev0.record(s)
             texts = []
             for r in batch:
                 if r.text is not None:
@@ -387,88 +443,128 @@ class Server:
             smg.search_batch_async_array(qarr, ws.data_ptr(), need, stream=s)
             cnt_h = torch.empty(len(batch), dtype=torch.int64, pin_memory=True)
             cnt_h.copy_(cnt, non_blocking=True)
-            ev = torch.cuda.Event()
+            ev = torch.cuda.Event(enable_timing=True)
             ev.record(s)
         t3 = time.perf_counter()
         self.host_s["h2d_own_texts"] += t1 - t0
         self.host_s["prepare"] += t2 - t1
         self.host_s["launch"] += t3 - t2
-        self.inflight[slot] = {"batch": batch, "event": ev, "cnt_h": cnt_h, "out_h": None,
-                               "offs": offs, "keep": (texts, plans, out, cnt, ws), "reserved": reserved,
-                               "phase": 0}
+        self.inflight[slot] = {"batch": batch, "event": ev, "ev0": ev0, "cnt_h": cnt_h, "offs": offs,
+                               "keep": (texts, plans, out, cnt, ws), "reserved": reserved, "phase": 0,
+                               "scan": sum(self.policy.scan_bytes(r) for r in batch)}
         self.batches += 1
 
+    def _complete(self, r: Request, pos, now: float) -> None:
+        lat = now - r.t_arrival
+        self.latencies.append(lat)
+        self.lat_by_class[length_class(r.m)].append(lat)
+        self.completed += 1
+        r.future.set_result(pos)
+
     def _copy_back(self, i: int, rec: dict) -> None:
-        """Counts are on the host: copy back exactly the valid positions of
-        each complete request (not the whole capacity), then an event.
-        Small results go through the stream's staging buffer, large ones
-        into a pinned block of their own."""
+        """Counts are on the host.  Requests whose output was truncated go
+        back to the front of the queue at once, with their exact count as
+        the capacity.  For the others exactly the valid positions are copied
+        back (not the whole capacity): the small results first, through the
+        stream's staging buffer, then one event; then each large result into
+        a pinned block of its own, each followed by its own event, so every
+        request completes as soon as its own positions are on the host."""
         torch = self._torch
         counts = rec["cnt_h"].numpy()
-        caps = np.array([r.cap for r in rec["batch"]], dtype=np.int64)
+        batch = rec["batch"]
+        caps = np.array([r.cap for r in batch], dtype=np.int64)
+        requeue = [j for j in range(len(batch)) if counts[j] > caps[j]]
+        for j in requeue:
+            batch[j].cap = int(counts[j])
+            batch[j].attempts += 1
+        if requeue:
+            with self._lock:
+                for j in reversed(requeue):
+                    self.policy.push(batch[j], front=True)
+                self.retries += len(requeue)
+            self._wake.set()
         take = np.where(counts <= caps, counts, 0)
         small = np.where(take < self.SMALL_RESULT, take, 0)
         dst_offs = np.concatenate([[0], np.cumsum(small)])
         out_h = self._staging[i]
         out = rec["keep"][2]
-        blocks = {}
+        large = []
         s = self.streams[i]
         with torch.cuda.stream(s):
-            for j in np.flatnonzero(take):
+            ev_c = torch.cuda.Event(enable_timing=True)
+            ev_c.record(s)
+            for j in np.flatnonzero(small):
+                a = int(rec["offs"][j])
+                out_h[int(dst_offs[j]):int(dst_offs[j + 1])].copy_(out[a:a + int(small[j])], non_blocking=True)
+            ev_small = torch.cuda.Event()
+            ev_small.record(s)
+            for j in np.flatnonzero(take >= self.SMALL_RESULT):
                 a = int(rec["offs"][j])
                 c = int(take[j])
-                if c < self.SMALL_RESULT:
-                    out_h[int(dst_offs[j]):int(dst_offs[j + 1])].copy_(out[a:a + c], non_blocking=True)
-                else:
-                    block, cls = self.pool.take(8 * c)
-                    if block is None:  # pool full: an ordinary host array (a blocking copy)
-                        blocks[j] = out[a:a + c].cpu().numpy().view(np.uint64)
-                        continue
-                    block[: 8 * c].view(torch.int64).copy_(out[a:a + c], non_blocking=True)
-                    blocks[j] = (block, cls)
-            ev = torch.cuda.Event()
-            ev.record(s)
-        rec.update(out_h=out_h, dst_offs=dst_offs, blocks=blocks, event=ev, phase=1)
+                block, cls = self.pool.take(8 * c)
+                if block is None:  # pool full: an ordinary host array (a blocking copy)
+                    large.append([j, out[a:a + c].cpu().numpy().view(np.uint64), None])
+                    continue
+                block[: 8 * c].view(torch.int64).copy_(out[a:a + c], non_blocking=True)
+                e = torch.cuda.Event()
+                e.record(s)
+                large.append([j, (block, cls), e])
+            ev_end = torch.cuda.Event(enable_timing=True)
+            ev_end.record(s)
+        todo = [j for j in range(len(batch)) if j not in set(requeue)]
+        rec.update(out_h=out_h, dst_offs=dst_offs, small=small, ev_small=ev_small, large=large,
+                   ev_c=ev_c, event=ev_end, phase=1, todo=set(todo), small_done=False,
+                   out_bytes=int(8 * take.sum()))
 
     def _retire(self) -> bool:
         done_any = False
         for i, rec in enumerate(self.inflight):
-            if rec is None or not rec["event"].query():
+            if rec is None:
                 continue
-            done_any = True
             if rec["phase"] == 0:
+                if not rec["event"].query():
+                    continue
+                done_any = True
                 tc = time.perf_counter()
                 self._copy_back(i, rec)
                 self.host_s["copy_back"] += time.perf_counter() - tc
                 continue
             now = time.perf_counter()
+            t_r = now
+            batch = rec["batch"]
             counts = rec["cnt_h"].numpy()
-            out_h = rec["out_h"].numpy()
-            offs = rec["dst_offs"]
-            requeue = []
-            for j, r in enumerate(rec["batch"]):
-                c = int(counts[j])
-                if c > r.cap:
-                    r.cap = c
-                    r.attempts += 1
-                    requeue.append(r)
-                    continue
-                if j in rec["blocks"]:
-                    b = rec["blocks"][j]
-                    pos = b if isinstance(b, np.ndarray) else self.pool.view(*b, c)  # no copy
-                else:
-                    # out of the stream's reusable staging buffer
-                    pos = out_h[int(offs[j]):int(offs[j]) + c].astype(np.uint64)
-                self.latencies.append(now - r.t_arrival)
-                self.completed += 1
-                r.future.set_result(pos)
+            if not rec["small_done"] and rec["ev_small"].query():
+                out_h = rec["out_h"].numpy()
+                offs = rec["dst_offs"]
+                for j in np.flatnonzero(rec["small"]):
+                    self._complete(batch[j], out_h[int(offs[j]):int(offs[j + 1])].astype(np.uint64), now)
+                    rec["todo"].discard(int(j))
+                for j in list(rec["todo"]):  # empty results
+                    if counts[j] == 0:
+                        self._complete(batch[j], np.zeros(0, dtype=np.uint64), now)
+                        rec["todo"].discard(j)
+                rec["small_done"] = True
+                done_any = True
+            for item in rec["large"]:
+                j, b, e = item
+                if j in rec["todo"] and (e is None or e.query()):
+                    pos = b if isinstance(b, np.ndarray) else self.pool.view(*b, int(counts[j]))  # no copy
+                    self._complete(batch[j], pos, now)
+                    rec["todo"].discard(j)
+                    done_any = True
+            if rec["todo"] or not rec["event"].query():
+                self.host_s["retire"] += time.perf_counter() - t_r
+                continue
+            # Whole batch done: measured scan and copy times update the
+            # policy's rate estimates; plans and memory are released.
+            scan_s = rec["ev0"].elapsed_time(rec["ev_c"]) / 1e3
+            copy_s = rec["ev_c"].elapsed_time(rec["event"]) / 1e3
             for p in rec["keep"][1]:
                 p.free()
             with self._lock:
+                self.policy.observe(rec["scan"], scan_s, rec["out_bytes"], copy_s)
                 self.policy.release(rec["reserved"])
-                for r in reversed(requeue):
-                    self.policy.push(r, front=True)
-                self.retries += len(requeue)
                 self.inflight[i] = None
-            self.host_s["retire"] += time.perf_counter() - now
+            done_any = True
+            self.host_s["retire"] += time.perf_counter() - t_r
         return done_any

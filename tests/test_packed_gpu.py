@@ -114,3 +114,53 @@ def test_moderately_dense_pack_lane_reextraction():
         exp = oracle.naive(t, p)
         assert cp[i] == len(exp)
         assert np.array_equal(packed[i], exp), len(p)
+
+
+def test_shared_long_text_interleaved_items():
+    """Queries of every kernel family on one 40 MiB text (long enough for the
+    batch to interleave their work items by text position) plus queries on
+    a second long text and on short texts, as one batch and as a replayed
+    graph: every result equals the oracle's."""
+    import torch
+
+    import paper_1012_2547_gb300 as smg
+    rng = np.random.default_rng(77)
+    n = 40 << 20
+    big = [rng.integers(0, 4, n, dtype=np.uint8), rng.integers(0, 64, n, dtype=np.uint8)]
+    big[0][: 1 << 20] = 0                                    # a dense stretch for a^m patterns
+    small = [rng.integers(0, 4, 300_000, dtype=np.uint8)]
+    texts = big + small
+    dev = [torch.from_numpy(t).cuda() for t in texts]
+    items = []
+    for ti, t in enumerate(texts):
+        for m in (2, 4, 8, 12, 16, 17, 24, 32, 40, 64, 100, 300, 1000):
+            for r in range(2):
+                o = int(rng.integers(0, len(t) - m))
+                items.append((ti, bytes(t[o:o + m])))
+        items.append((ti, bytes(17)))                        # a^17: dense where t is 0
+        items.append((ti, bytes(100)))
+    plans = [smg.prepare(p, sigma_hint=4 if ti != 1 else 64) for ti, p in items]
+    cnt = torch.zeros(len(items), dtype=torch.int64, device="cuda")
+    smg.search_batch([(dev[ti], plans[i], None, cnt[i:i + 1]) for i, (ti, _) in enumerate(items)])
+    smg.sync()
+    c = cnt.cpu().numpy()
+    offs = np.concatenate([[0], np.cumsum(c)])
+    for graph in (False, True):
+        out = torch.full((max(int(c.sum()), 1),), -1, dtype=torch.int64, device="cuda")
+        cnt2 = torch.zeros_like(cnt)
+        qs = [(dev[ti], plans[i], out[int(offs[i]):int(offs[i + 1])], cnt2[i:i + 1]) for i, (ti, _) in enumerate(items)]
+        if graph:
+            b = smg.Batch(qs, graph=True)
+            b.launch()
+            b.launch()
+            smg.sync()
+            b.free()
+        else:
+            smg.search_batch(qs)
+            smg.sync()
+        host = out.cpu().numpy().astype(np.uint64)
+        assert torch.equal(cnt, cnt2)
+        for i, (ti, p) in enumerate(items):
+            exp = oracle.kmp(texts[ti], p)
+            assert int(c[i]) == len(exp), (ti, len(p))
+            assert np.array_equal(host[int(offs[i]):int(offs[i + 1])], exp), (ti, len(p), graph)

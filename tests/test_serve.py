@@ -102,6 +102,25 @@ def test_pinned_pool_size_classes():
         assert c <= 1.25 * max(n, PinnedPool.MIN_BYTES) + 1     # under a fifth wasted
 
 
+def test_batch_time_bound_and_rates():
+    """A batch's estimated GPU time (scan bytes / scan rate + output bytes /
+    copy rate) stays under max_batch_seconds, one step per scan_backlog
+    pending requests; measured batches move the rates."""
+    p = Policy(budget_bytes=1 << 40, max_batch=100, workspace_per_batch=0, corpus_bytes={"c": 1 << 30},
+               max_batch_seconds=0.001, scan_rate=1e12, copy_rate=1e11, scan_backlog=100)
+    for i in range(5):
+        p.push(req(i, 8, cap=1000))            # 1.07 ms of scan each: one per batch
+    b, _, _ = p.take()
+    assert [r.rid for r in b] == [0]
+    p.max_batch_seconds = 0.0025
+    b, _, _ = p.take()
+    assert [r.rid for r in b] == [1, 2]
+    p.observe(4 << 30, 0.002, 0, 0.0)         # 2.1 TB/s measured: the estimate moves up
+    assert 1e12 < p.scan_rate <= 1e12 * 1.25
+    p.observe(4 << 30, 1e-9, 0, 0.0)           # an outlier counts at most 4x
+    assert p.scan_rate <= 1e12 * 1.25 * 1.6
+
+
 def test_ready_rules():
     p = Policy(budget_bytes=1 << 30, max_batch=2, max_wait=0.01)
     assert not p.ready(0.0, busy=0)
@@ -139,7 +158,10 @@ def test_server_results_equal_alone_and_in_mix():
             p = gen.substring_patterns(t, min(m, n), 1, seed=k)[0] if n >= m else bytes(m)
             reqs.append((p, None, t, t))
     reqs.append((b"\x00\x01", "rand4", None, corp4))          # dense: triggers a retry
-    srv = Server(dev, budget_bytes=2 << 30, streams=3, max_batch=64, sigma_hints={"rand4": 4, "english": 90})
+    # cap_factor 0: first attempts get only first_cap positions, so dense
+    # results take the truncation-and-retry path.
+    srv = Server(dev, budget_bytes=2 << 30, streams=3, max_batch=64, sigma_hints={"rand4": 4, "english": 90},
+                 cap_factor=0.0)
     futs = []
     for i, (p, name, own, _) in enumerate(reqs):
         futs.append(srv.submit(p, corpus=name, text=own))

@@ -996,6 +996,8 @@ def serve_record(args, local, loads=None) -> dict:
         by_load[str(frac)] = {"offered_qps": round(frac * sat["qps"], 1), "qps": st["qps"],
                             "served_over_offered": round(st["qps"] / (frac * sat["qps"]), 3),
                             "p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
+                            "queue_p50_ms": st["queue_p50_ms"], "queue_p99_ms": st["queue_p99_ms"],
+                            "host_max_ms": st["host_max_ms"],
                             "by_length_class": st["by_length_class"], "batches": st["batches"],
                             "retries": st["retries"], "rates": st["rates"], "host_s": st["host_s"]}
     out = {

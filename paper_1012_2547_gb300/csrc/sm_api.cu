@@ -586,6 +586,11 @@ struct PinnedStaging {
     std::mutex mu;
     uint8_t *p = nullptr;
     size_t cap = 0;
+    // Buffers outgrown are kept, not freed: cudaFreeHost waits for the whole
+    // device, which stalled a serving loop's scheduler for tens of
+    // milliseconds.  Growth doubles, so they add up to less than the buffer
+    // in use.
+    std::vector<uint8_t *> outgrown;
 };
 
 PinnedStaging &pinned_staging() {
@@ -639,14 +644,13 @@ sm_status prepare_many(const uint8_t *patterns, const uint32_t *lengths, uint32_
     std::vector<uint8_t> pageable;
     if (total <= kStagingMax) {
         if (ps.cap < total) {
-            if (ps.p) cudaFreeHost(ps.p);
-            ps.p = nullptr;
-            ps.cap = 0;
-            const size_t want = std::min(kStagingMax, std::max<size_t>(total + total / 2, size_t(16) << 20));
-            if (cudaHostAlloc(reinterpret_cast<void **>(&ps.p), want, cudaHostAllocDefault) == cudaSuccess) {
+            const size_t want = std::min(kStagingMax, std::max({total + total / 2, 2 * ps.cap, size_t(64) << 20}));
+            uint8_t *np = nullptr;
+            if (cudaHostAlloc(reinterpret_cast<void **>(&np), want, cudaHostAllocDefault) == cudaSuccess) {
+                if (ps.p) ps.outgrown.push_back(ps.p);
+                ps.p = np;
                 ps.cap = want;
             } else {
-                ps.p = nullptr;
                 (void)cudaGetLastError();  // not sticky: stage in pageable memory instead
             }
         }

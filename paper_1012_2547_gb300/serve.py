@@ -27,7 +27,8 @@ thread repeatedly
 
 A first attempt's output capacity is sized from the count expected for the
 pattern's bytes under the text's byte frequencies, so few requests need a
-second attempt.  Up to ``streams`` batches are in flight at once, so
+second attempt.  A request's own text is copied into pinned memory by the
+caller's thread at submission, so the scheduler uploads it asynchronously.  Up to ``streams`` batches are in flight at once, so
 requests that arrive while others run are admitted as slots and memory
 free up and their work overlaps on the device.  Every request records
 arrival and completion times (p50 / p99 latency, also per length class).
@@ -63,6 +64,8 @@ class Request:
     t_arrival: float
     future: cf.Future = field(default_factory=cf.Future)
     attempts: int = 0
+    t_launch: float = 0.0  # host time its (last) batch was launched
+    staged: tuple | None = None  # (pinned block, size class) holding its own text
 
     @property
     def m(self) -> int:
@@ -291,6 +294,7 @@ class Server:
                              max_batch_seconds=max_batch_seconds)
         self.lat_by_class = collections.defaultdict(list)
         self.streams = [torch.cuda.Stream() for _ in range(streams)]
+        self._prep_stream = torch.cuda.Stream()
         self.inflight: list[dict | None] = [None] * streams
         # Per-stream pinned staging for the copy-back of small results
         # (at most max_batch * SMALL_RESULT positions a batch), allocated up
@@ -305,6 +309,8 @@ class Server:
         self.pool = PinnedPool.shared(torch, budget_bytes + (8 << 30) if pinned_pool_bytes is None
                                       else pinned_pool_bytes)
         self.latencies: list[float] = []
+        self.queue_s: list[float] = []   # arrival -> launch of the batch that completed it
+        self.host_max = collections.Counter()  # longest single scheduler phase, seconds
         self.completed = 0
         self.retries = 0
         self.batches = 0
@@ -334,6 +340,14 @@ class Server:
         n = len(t) if t is not None else self.corpora[corpus].numel()
         r = Request(next(self._ids), p, corpus, t, self._first_cap(n, p, corpus, t),
                     time.perf_counter() if t_arrival is None else t_arrival)
+        if t is not None and len(t):
+            # The caller's thread copies its text into a pinned block, so the
+            # scheduler uploads it asynchronously instead of copying from
+            # pageable memory itself (which blocked it for up to ~10 ms).
+            block, cls = self.pool.take(len(t))
+            if block is not None:
+                block[: len(t)].numpy()[:] = t
+                r.staged = (block, cls)
         with self._lock:
             self.policy.push(r)
         self._wake.set()
@@ -369,9 +383,13 @@ class Server:
             a = np.array(v)
             by_class[f"m{1 << c}-{(2 << c) - 1}"] = {"n": len(v), "p50_ms": round(float(np.percentile(a, 50)) * 1e3, 3),
                                                   "p99_ms": round(float(np.percentile(a, 99)) * 1e3, 3)}
+        qs = np.array(self.queue_s) if self.queue_s else np.zeros(1)
         return {"completed": self.completed, "batches": self.batches, "retries": self.retries,
                 "pinned_pool_bytes": self.pool.allocated_bytes,
                 "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "queue_p50_ms": round(float(np.percentile(qs, 50)) * 1e3, 3),
+                "queue_p99_ms": round(float(np.percentile(qs, 99)) * 1e3, 3),
+                "host_max_ms": {k: round(v * 1e3, 3) for k, v in self.host_max.items()},
                 "by_length_class": by_class,
                 "rates": {"scan_GBs": round(self.policy.scan_rate / 1e9, 1),
                           "copy_GBs": round(self.policy.copy_rate / 1e9, 1)},
@@ -392,6 +410,9 @@ class Server:
                         batch, reserved, rejected = self.policy.take()
                     idle = not self.policy.pending and busy == 0
                 for r in rejected:
+                    if r.staged is not None:
+                        self.pool._give(*r.staged)
+                        r.staged = None
                     r.future.set_exception(MemoryError("request larger than the device budget"))
                 if batch:
                     self._launch(slot, batch, reserved)
@@ -421,13 +442,17 @@ class Server:
             ev0.record(s)
             texts = []
             for r in batch:
-                if r.text is not None:
+                if r.staged is not None:
+                    texts.append(r.staged[0][: len(r.text)].to(dev, non_blocking=True))
+                elif r.text is not None:
                     texts.append(torch.from_numpy(r.text).to(dev, non_blocking=False))
                 else:
                     texts.append(self.corpora[r.corpus])
             t1 = time.perf_counter()
             hint = self.sigma_hints.get(batch[0].corpus, self.own_text_sigma)
-            plans = smg.prepare_many([r.pattern for r in batch], sigma_hint=hint)
+            # Plans upload on a stream of their own: prepare_many waits for
+            # its stream, which must not hold this batch's text uploads.
+            plans = smg.prepare_many([r.pattern for r in batch], sigma_hint=hint, stream=self._prep_stream)
             t2 = time.perf_counter()
             caps = np.array([r.cap for r in batch], dtype=np.int64)
             offs = np.concatenate([[0], np.cumsum(caps)])
@@ -446,17 +471,23 @@ class Server:
             ev = torch.cuda.Event(enable_timing=True)
             ev.record(s)
         t3 = time.perf_counter()
-        self.host_s["h2d_own_texts"] += t1 - t0
-        self.host_s["prepare"] += t2 - t1
-        self.host_s["launch"] += t3 - t2
+        for r in batch:
+            r.t_launch = t0
+        for k, v in (("h2d_own_texts", t1 - t0), ("prepare", t2 - t1), ("launch", t3 - t2)):
+            self.host_s[k] += v
+            self.host_max[k] = max(self.host_max[k], v)
         self.inflight[slot] = {"batch": batch, "event": ev, "ev0": ev0, "cnt_h": cnt_h, "offs": offs,
                                "keep": (texts, plans, out, cnt, ws), "reserved": reserved, "phase": 0,
                                "scan": sum(self.policy.scan_bytes(r) for r in batch)}
         self.batches += 1
 
     def _complete(self, r: Request, pos, now: float) -> None:
+        if r.staged is not None:  # its upload finished before its search ran
+            self.pool._give(*r.staged)
+            r.staged = None
         lat = now - r.t_arrival
         self.latencies.append(lat)
+        self.queue_s.append(r.t_launch - r.t_arrival)
         self.lat_by_class[length_class(r.m)].append(lat)
         self.completed += 1
         r.future.set_result(pos)
@@ -527,7 +558,9 @@ class Server:
                 done_any = True
                 tc = time.perf_counter()
                 self._copy_back(i, rec)
-                self.host_s["copy_back"] += time.perf_counter() - tc
+                dt = time.perf_counter() - tc
+                self.host_s["copy_back"] += dt
+                self.host_max["copy_back"] = max(self.host_max["copy_back"], dt)
                 continue
             now = time.perf_counter()
             t_r = now

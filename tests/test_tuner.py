@@ -73,3 +73,26 @@ def test_builtin_choice_rule():
     for m in (8, 40, 100, 1024):
         for sg in (2, 4, 20, 128):
             assert tuner.builtin(m, sg) in tuner.candidates(m)
+
+
+def test_library_sigma_buckets():
+    """The library reads the cell of floor(log2 sigma): a config put in the
+    sigma = 4 cell of m = 32 serves sigma hints 4 to 7, the sigma = 2 cell
+    serves 2 and 3, the sigma = 8 cell 8 (no GPU: plan images only)."""
+    import paper_1012_2547_gb300 as smg
+    cells = [{"variant": 0, "q": 0, "word_bits": 0, "tile": 0} for _ in range(tuner.M_BUCKETS * tuner.S_BUCKETS)]
+    mb = tuner.m_bucket(32)
+    cells[mb * tuner.S_BUCKETS + 1] = {"variant": 1, "q": 0, "word_bits": 64, "tile": 0}
+    cells[mb * tuner.S_BUCKETS + 2] = {"variant": 2, "q": 5, "word_bits": 0, "tile": 0}
+    cells[mb * tuner.S_BUCKETS + 3] = {"variant": 2, "q": 7, "word_bits": 0, "tile": 0}
+    smg.tuning_set(cells)
+    try:
+        p = bytes(range(32))
+        got = {sg: smg.plan_image(p, sigma_hint=sg)[1] for sg in (2, 3, 4, 7, 8)}
+        for sg in (2, 3):
+            assert got[sg]["variant"] == "shiftor" and got[sg]["word_bits"] == 64, sg
+        for sg in (4, 7):
+            assert got[sg]["variant"] == "qgram" and got[sg]["q"] == 5, sg
+        assert got[8]["variant"] == "qgram" and got[8]["q"] == 7
+    finally:
+        smg.tuning_reset()

@@ -1119,7 +1119,13 @@ def main():
             # compact form, so one default run reports every half of the
             # metric (each also runs alone: --workload bandwidth / serve).
             out["bandwidth"] = bandwidth_record(args, local, compact=True)
+            # The committed tuning table is measured on the sweep's 4 MiB
+            # texts; the server's 2 GiB corpora run with the built-in rule,
+            # as in the standalone serving bench.
+            import paper_1012_2547_gb300 as smg
+            smg.tuning_reset()
             out["serve"] = serve_record(args, local, loads=[0.5, 0.8, 0.95])
+            out["serve"]["kernel_choice"] = "built-in rule (tuning table reset)"
         if rank == 0:
             print(json.dumps(out), flush=True)
     finally:

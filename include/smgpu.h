@@ -168,9 +168,12 @@ sm_status sm_plan_info(const sm_plan *plan, sm_plan_desc *out);
  *   qgram_*    : QGRAM plans.  slots: 1 << slot_bits entries of {u64 key
  *                (q-gram, byte 0 in bits 0..7), u32 first, u32 count}
  *                (count 0 = empty); offsets: u32, the offsets j of each key
- *                at [first, first + count) in decreasing order; bitmap:
- *                1 << bitmap_bits bits, bit (key * 0x9E3779B97F4A7C15) >>
- *                (64 - bitmap_bits) set for every key.
+ *                at [first, first + count) in decreasing order; slot of a
+ *                key: (key * 0x9E3779B97F4A7C15) >> (64 - slot_bits), then
+ *                linear probing; bitmap: 1 << bitmap_bits bits, bit
+ *                h >> (32 - bitmap_bits) set for every key, with the 32-bit
+ *                h = (lo * 0x9E3779B1) ^ (hi * 0x85EBCA77), lo and hi the
+ *                key's low and high 32 bits.
  *   automaton  : DFA plans, and QGRAM plans of periodic patterns (smallest
  *                period <= m/2) whose table fits.  classes_tab: u16[256],
  *                2 x the class of each byte (class 0: bytes absent from p);

@@ -465,7 +465,12 @@ sm_status build_blob(const uint8_t *p, uint32_t m, uint32_t sigma, const sm_conf
             while (slots[sl].count && slots[sl].key != g) sl = (sl + 1) & mask;
             if (!slots[sl].count) {
                 slots[sl].key = g;
-                const uint32_t bb = static_cast<uint32_t>(hh >> (64 - h.bm_bits));
+                // Bitmap bit: top bm_bits bits of the two 32-bit halves'
+                // multiplicative hashes xored (the same function as the
+                // kernel's probe loop).
+                const uint32_t h32 = (static_cast<uint32_t>(g) * 0x9E3779B1u) ^
+                                     (static_cast<uint32_t>(g >> 32) * 0x85EBCA77u);
+                const uint32_t bb = h32 >> (32 - h.bm_bits);
                 bitmap[bb >> 5] |= 1u << (bb & 31);
             }
             ++slots[sl].count;

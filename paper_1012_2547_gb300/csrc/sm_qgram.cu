@@ -82,7 +82,17 @@ struct QGCtl {
     uint32_t ok;
 };
 
+// Hash of a packed q-gram for the key table's slots (64-bit golden-ratio
+// multiplicative hashing).
 __device__ __forceinline__ uint64_t qgram_hash(uint64_t g) { return g * 0x9E3779B97F4A7C15ull; }
+
+// Hash of a packed q-gram (lo: bytes 0..3, hi: bytes 4..7) for the presence
+// bitmap, whose bit is its top bm_bits bits: two 32-bit multiplicative
+// hashes (the golden-ratio constant 0x9E3779B1 and xxHash32's second prime
+// 0x85EBCA77) xored, two IMADs and one LOP in the probe loop.
+__device__ __forceinline__ uint32_t qgram_bitmap_hash(uint32_t lo, uint32_t hi) {
+    return (lo * 0x9E3779B1u) ^ (hi * 0x85EBCA77u);
+}
 
 // Bytes t[pos..pos+q-1] packed little-endian; t[pos+q-1] must be in the text.
 __device__ __forceinline__ uint64_t load_qgram(const uint8_t *t, uint64_t pos, uint32_t q) {
@@ -348,41 +358,50 @@ __device__ bool qgram_warp(const PlanView &v, uint64_t patw, const uint8_t *text
     const uint64_t s = v.s;
     const uint64_t k0 = Lw / s;
     const uint64_t kend = min(k0 + span / s, (n - v.m) / s + 1);  // probes [k0, kend) hold valid starts
-    const uint64_t nr = kend > k0 ? (kend - k0 + 31) / 32 : 0;
-    const uint64_t qmask = v.q >= 8 ? ~0ull : ((1ull << (8u * v.q)) - 1ull);
+    // Probe k0 + j sits at first + j * s; j and j * s fit in 32 bits (a
+    // warp's span is below 2^32 starts).
+    const uint32_t np = kend > k0 ? static_cast<uint32_t>(kend - k0) : 0u;
+    const uint32_t nr = (np + 31u) / 32u;
+    const uint32_t s32 = static_cast<uint32_t>(s);
+    const uintptr_t first = reinterpret_cast<uintptr_t>(text) + k0 * s + (s - 1u);
+    const uint32_t q = v.q;
+    const uint32_t mlo = q >= 4 ? 0xFFFFFFFFu : ((1u << (8u * q)) - 1u);
+    const uint32_t mhi = q >= 8 ? 0xFFFFFFFFu : q <= 4 ? 0u : ((1u << (8u * (q - 4u))) - 1u);
+    const uint32_t bshift = 32u - v.bm_bits;
     run = QGRun{0, 0, 0};
-    for (uint64_t r0 = 0; r0 < nr; r0 += QG_U) {
+    for (uint32_t r0 = 0; r0 < nr; r0 += QG_U) {
         // Every load of the QG_U rounds is issued before any of their words
-        // is used: the two aligned words that hold each probe's q-gram (the
-        // second only when the q-gram reaches into it), then the bitmap
-        // words; one vote decides whether any of the rounds needs the table.
-        uint64_t lo[QG_U], hi[QG_U];
-        uint32_t sh[QG_U];
+        // is used: the aligned 32-bit words that hold each probe's q-gram
+        // (the second and third only when the q-gram reaches into them),
+        // then the bitmap words; one vote decides whether any of the rounds
+        // needs the key table.
+        uint32_t w0[QG_U], w1[QG_U], w2[QG_U], sh[QG_U];
 #pragma unroll
         for (int u = 0; u < QG_U; ++u) {
-            const uint64_t kp = k0 + (r0 + u) * 32u + lane;
-            const bool live = kp < kend;
-            const uintptr_t addr = reinterpret_cast<uintptr_t>(text) + (live ? kp * s + s - 1u : 0u);
-            const uint64_t *w = reinterpret_cast<const uint64_t *>(addr & ~uintptr_t(7));
-            sh[u] = static_cast<uint32_t>(addr & 7u);
-            lo[u] = live ? __ldg(w) : 0ull;
-            hi[u] = live && sh[u] + v.q > 8u ? __ldg(w + 1) : 0ull;
+            const uint32_t j = (r0 + u) * 32u + lane;
+            const bool live = j < np;
+            const uintptr_t addr = first + (live ? static_cast<uint64_t>(j) * s32 : 0u);
+            const uint32_t *w = reinterpret_cast<const uint32_t *>(addr & ~uintptr_t(3));
+            const uint32_t b = static_cast<uint32_t>(addr & 3u);
+            sh[u] = 8u * b;
+            w0[u] = live ? __ldg(w) : 0u;
+            w1[u] = live && b + q > 4u ? __ldg(w + 1) : 0u;
+            w2[u] = live && b + q > 8u ? __ldg(w + 2) : 0u;
         }
-        uint64_t g[QG_U];
         uint32_t bw[QG_U], bb[QG_U];
 #pragma unroll
         for (int u = 0; u < QG_U; ++u) {
-            const uint32_t b = 8u * sh[u];
-            g[u] = (b ? (lo[u] >> b) | (hi[u] << (64u - b)) : lo[u]) & qmask;
-            const uint32_t hb = static_cast<uint32_t>(qgram_hash(g[u]) >> (64u - v.bm_bits));
+            const uint32_t lo = __funnelshift_r(w0[u], w1[u], sh[u]) & mlo;
+            const uint32_t hi = __funnelshift_r(w1[u], w2[u], sh[u]) & mhi;
+            const uint32_t hb = qgram_bitmap_hash(lo, hi) >> bshift;
             bb[u] = hb & 31u;
             bw[u] = __ldg(&v.bitmap[hb >> 5]);
         }
         uint32_t hits = 0;  // bit u: round u passes the bitmap on this lane
 #pragma unroll
         for (int u = 0; u < QG_U; ++u) {
-            const uint64_t kp = k0 + (r0 + u) * 32u + lane;
-            hits |= (kp < kend && ((bw[u] >> bb[u]) & 1u)) ? (1u << u) : 0u;
+            const uint32_t j = (r0 + u) * 32u + lane;
+            hits |= (j < np && ((bw[u] >> bb[u]) & 1u)) ? (1u << u) : 0u;
         }
         if (!__any_sync(0xffffffffu, hits != 0)) continue;
 #pragma unroll 1

@@ -114,14 +114,17 @@ def test_qgram_table_is_exact(m, q):
         offs = u32(img, lay["off_qgram_offsets"], m - q + 1)
         bitmap = u32(img, lay["off_qgram_bitmap"], (1 << lay["bitmap_bits"]) // 32)
         got = {}
+        bits = set()
         for sl in slots[slots["count"] > 0]:
             key = int(sl["key"])
             assert key not in got
             got[key] = list(offs[sl["first"]: sl["first"] + sl["count"]])
-            h = (key * 0x9E3779B97F4A7C15) & ((1 << 64) - 1)
-            b = h >> (64 - lay["bitmap_bits"])
+            h = (((key & 0xFFFFFFFF) * 0x9E3779B1) ^ ((key >> 32) * 0x85EBCA77)) & 0xFFFFFFFF
+            b = h >> (32 - lay["bitmap_bits"])
             assert (int(bitmap[b >> 5]) >> (b & 31)) & 1
+            bits.add(b)
         assert got == {k: sorted(v, reverse=True) for k, v in want.items()}
+        assert sum(bin(int(w)).count("1") for w in bitmap) == len(bits)   # no other bit set
 
 
 def simulate(img, lay, text):

@@ -82,6 +82,12 @@ struct QGCtl {
     uint32_t ok;
 };
 
+__device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+
 // Hash of a packed q-gram for the key table's slots (64-bit golden-ratio
 // multiplicative hashing).
 __device__ __forceinline__ uint64_t qgram_hash(uint64_t g) { return g * 0x9E3779B97F4A7C15ull; }
@@ -110,6 +116,7 @@ __device__ __forceinline__ uint64_t load_qgram(const uint8_t *t, uint64_t pos, u
 struct PlanView {
     const uint8_t *pat;
     const uint32_t *bitmap;
+    uint32_t bm_smem;  // shared-memory address of the bitmap's copy (q-gram kernel), else 0
     const QSlot *slots;
     const uint32_t *offs;
     const uint32_t *fail;
@@ -127,6 +134,7 @@ __device__ __forceinline__ PlanView plan_view(const PlanDev *P) {
     v.slot_bits = __ldg(&P->slot_bits);
     v.pat = b + __ldg(&P->off_pat);
     v.bitmap = reinterpret_cast<const uint32_t *>(b + __ldg(&P->off_bitmap));
+    v.bm_smem = 0;
     v.slots = reinterpret_cast<const QSlot *>(b + __ldg(&P->off_slots));
     v.offs = reinterpret_cast<const uint32_t *>(b + __ldg(&P->off_offs));
     v.fail = reinterpret_cast<const uint32_t *>(b + __ldg(&P->off_fail));
@@ -395,7 +403,7 @@ __device__ bool qgram_warp(const PlanView &v, uint64_t patw, const uint8_t *text
             const uint32_t hi = __funnelshift_r(w1[u], w2[u], sh[u]) & mhi;
             const uint32_t hb = qgram_bitmap_hash(lo, hi) >> bshift;
             bb[u] = hb & 31u;
-            bw[u] = __ldg(&v.bitmap[hb >> 5]);
+            bw[u] = lds_u32(v.bm_smem + 4u * (hb >> 5));
         }
         uint32_t hits = 0;  // bit u: round u passes the bitmap on this lane
 #pragma unroll
@@ -507,6 +515,7 @@ __global__ void __launch_bounds__(QG_THREADS) qg_kernel(const LaunchArgs a) {
     __shared__ __align__(16) uint8_t dfa_raw[MODE == QG_DFA ? sizeof(DfaShared) : 16];
     __shared__ __align__(16) uint8_t qgw_raw[MODE == QG_QGRAM ? sizeof(QGWarp) * (QG_THREADS / 32) : 16];
     QGWarp *qgw = reinterpret_cast<QGWarp *>(qgw_raw);
+    __shared__ __align__(16) uint32_t qbm[MODE == QG_QGRAM ? (1u << 16) / 32 : 4];
     DfaShared &dsm = *reinterpret_cast<DfaShared *>(dfa_raw);
     const PlanDev *loaded = nullptr;  // plan whose automaton is in shared memory
     const int tid = threadIdx.x;
@@ -530,12 +539,24 @@ __global__ void __launch_bounds__(QG_THREADS) qg_kernel(const LaunchArgs a) {
         if (ctl.ticket >= a.total) break;
         const QueryDev &Q = query_of(a, ctl.qi);
         const uint64_t k = ctl.tile;
-        const PlanView v = plan_view(Q.plan);
+        PlanView v = plan_view(Q.plan);
+        if (MODE == QG_QGRAM) v.bm_smem = smem_addr(qbm);
         const uint64_t R = static_cast<uint64_t>(__ldg(&Q.plan->tile_starts) / QG_THREADS) *
                            Q.sub_per_item;
         const uint64_t L = k * R * QG_THREADS + static_cast<uint64_t>(tid) * R;
         const uint8_t *text = Q.text;
         const uint64_t n = Q.n;
+        if (MODE == QG_QGRAM && Q.plan != loaded) {
+            // The plan's presence bitmap (at most 2^16 bits) goes to shared
+            // memory: the probe loop's bitmap loads then never compete with
+            // the text streaming through L1.  Every thread is past its last
+            // use of the previous one (barrier at the end of the item).
+            const uint4 *src = reinterpret_cast<const uint4 *>(v.bitmap);
+            uint4 *dst = reinterpret_cast<uint4 *>(qbm);
+            for (uint32_t i = tid; i < (1u << v.bm_bits) / 128u; i += QG_THREADS) dst[i] = __ldg(src + i);
+            loaded = Q.plan;
+            __syncthreads();
+        }
         if (MODE == QG_DFA && Q.plan != loaded) {
             // Every thread is past its last use of the previous automaton
             // (barrier at the end of the previous item).  Blob offsets and

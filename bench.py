@@ -245,7 +245,8 @@ def sweep_kwargs(args) -> dict:
 
 KERNEL_NAMES = ["so_kernel<u32,u8,H>", "so_kernel<u32,u16,H>", "so_kernel<u32,u32,H>",
                 "so_kernel<u32,u32,A>", "so_kernel<u64,u64,H>", "so_kernel<u64,u64,A>",
-                "qg_kernel<qgram>", "qg_kernel<linear>"]
+                "qg_kernel<qgram>", "qg_kernel<linear>", "mp_kernel", "qg_kernel<dfa>",
+                "so_kernel<u32,u8,H,pair>"]
 
 
 def family_key(plan) -> int:

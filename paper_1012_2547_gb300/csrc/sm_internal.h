@@ -14,7 +14,7 @@ namespace smgpu {
 // 4 or 8 bytes) and how match flags are read ("H": 16 flags kept above bit
 // m-1 of the state; "A": accumulator plus rescan of flagged chunks).
 enum KernelId : int {
-    K_SO8H = 0,   // 32-bit state, byte masks, m <= 8
+    K_SO8H = 0,   // 32-bit state, byte masks, m = 7..8 (m <= 8 where asked by id)
     K_SO16H = 1,  // 32-bit state, half-word masks, m <= 16
     K_SO32H = 2,  // 32-bit state, word masks, m <= 17
     K_SO32A = 3,  // 32-bit state, word masks, m <= 32
@@ -24,21 +24,26 @@ enum KernelId : int {
     K_LINEAR = 7, // per-segment Knuth-Morris-Pratt
     K_SOMULTI = 8, // several Shift-And patterns (m <= 16) of one text in one state (batches only)
     K_DFA = 9,     // per-segment string-matching automaton, table in shared memory
-    K_COUNT = 10
+    K_SO6P = 10,   // 32-bit state, byte masks, two text bytes per step, m <= 6
+    K_COUNT = 11
 };
 
-inline bool so_kid(int kid) { return kid <= K_SO64A; }
+// The bit-parallel kernels (staged sub-tiles, one-warp blocks).  Patterns
+// of m <= 6 and 7..8 have kernels of their own (two-byte and one-byte
+// steps), so a launch holds one scan loop's code, not both.
+inline bool so_kid(int kid) { return kid <= K_SO64A || kid == K_SO6P; }
 // Kernels that stage sub-tiles and use the per-block spill area.
-inline bool staged_kid(int kid) { return kid <= K_SO64A || kid == K_SOMULTI; }
+inline bool staged_kid(int kid) { return so_kid(kid) || kid == K_SOMULTI; }
 inline uint32_t so_entry_bytes(int kid) {
-    return kid == K_SO8H ? 1u : kid == K_SO16H ? 2u : (kid <= K_SO32A ? 4u : 8u);
+    return kid == K_SO8H || kid == K_SO6P ? 1u : kid == K_SO16H ? 2u : (kid <= K_SO32A ? 4u : 8u);
 }
-inline uint32_t so_word_bits(int kid) { return kid <= K_SO32A ? 32u : 64u; }
+inline uint32_t so_word_bits(int kid) { return kid <= K_SO32A || kid == K_SO6P ? 32u : 64u; }
 inline bool so_hist(int kid) { return kid != K_SO32A && kid != K_SO64A; }
 // Bit-parallel kernel for length m and state width wb (0 = choose), or -1.
 inline int so_kid_for(uint32_t m, uint32_t wb) {
     if (wb == 0) wb = m <= 32 ? 32u : 64u;
-    if (wb == 32) return m <= 8 ? K_SO8H : m <= 16 ? K_SO16H : m <= 17 ? K_SO32H : m <= 32 ? K_SO32A : -1;
+    if (wb == 32)
+        return m <= 6 ? K_SO6P : m <= 8 ? K_SO8H : m <= 16 ? K_SO16H : m <= 17 ? K_SO32H : m <= 32 ? K_SO32A : -1;
     if (wb == 64) return m <= 49 ? K_SO64H : m <= 64 ? K_SO64A : -1;
     return -1;
 }

@@ -460,10 +460,12 @@ __device__ __forceinline__ void so_write_flags(const uint32_t (&F)[SO_SEGC], uin
 // copied out.  Two hit buffers and two spill areas alternate between the
 // item being scanned and the item waiting for its prefix.  Without a spill
 // area an item whose hits overflow the buffer is rescanned at write time.
-template <typename Word, typename Entry, bool HIST, int WARM>
+template <typename Word, typename Entry, bool HIST, int WARM, bool PAIR = false>
 __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchArgs a) {
     using L = SOLayout<Entry>;
-    constexpr bool PAIR_OK = sizeof(Word) == 4 && sizeof(Entry) == 1 && HIST && WARM != 0;
+    static_assert(!PAIR || (sizeof(Word) == 4 && sizeof(Entry) == 1 && HIST && WARM != 0),
+                  "two-byte steps need byte tables, a 32-bit state and the warm-up form");
+    constexpr bool PAIR_OK = PAIR;
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(256) uint8_t tbl[256 * sizeof(Entry) + (sizeof(Entry) == 1 ? 256 : 0)];
     const uint32_t tb = smem_addr(tbl);
@@ -608,7 +610,7 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
         // ring slot that no prefetch uses, writing each sub-tile's hits at
         // their final offsets.
         so_table<Entry>(Q.plan, cur_plan, tbl, m);
-        const bool pair = PAIR_OK && m <= 6;
+        constexpr bool pair = PAIR_OK;
         const uint64_t qn = Q.n;
         const int64_t vlo = o + static_cast<int64_t>(m) - 1;
         const int64_t vhi = o + static_cast<int64_t>(qn);
@@ -643,7 +645,7 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
     while (t < a.total) {
         const QueryDev &Q = query_of(a, qi);
         so_table<Entry>(Q.plan, cur_plan, tbl, m);
-        const bool pair = PAIR_OK && m <= 6;  // two bytes per step (see so_step4)
+        constexpr bool pair = PAIR_OK;  // two bytes per step (see so_step4); the plan's m <= 6
         // Query fields in registers: the mbarrier waits are compiler
         // barriers, after which descriptor fields would be reloaded.
         const uint8_t *const qtext = Q.text;
@@ -1210,6 +1212,7 @@ __global__ void __launch_bounds__(32) mp_kernel(const __grid_constant__ LaunchAr
 
 const void *so_kernel_fn(int kid) {
     switch (kid) {
+        case K_SO6P: return reinterpret_cast<const void *>(&so_kernel<uint32_t, uint8_t, true, 8, true>);
         case K_SO8H: return reinterpret_cast<const void *>(&so_kernel<uint32_t, uint8_t, true, 8>);
         case K_SO16H: return reinterpret_cast<const void *>(&so_kernel<uint32_t, uint16_t, true, 16>);
         case K_SO32H: return reinterpret_cast<const void *>(&so_kernel<uint32_t, uint32_t, true, 16>);
@@ -1281,7 +1284,7 @@ struct NoAllocDevice {
     bool ready = false;
     uint8_t *scratch = nullptr;  // device address of g_noalloc_scratch
     int sms = 0;
-    int bps[6] = {1, 1, 1, 1, 1, 1};  // resident blocks per SM of the six kernels
+    int bps[smgpu::K_COUNT] = {};  // resident blocks per SM of the bit-parallel kernels
 };
 
 std::mutex g_noalloc_mu;
@@ -1330,7 +1333,8 @@ sm_status na_setup(NoAllocDevice **out) {
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SM_ECUDA;
         if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return SM_ECUDA;
-        for (int k = 0; smgpu::so_kid(k); ++k) {
+        for (int k = 0; k < smgpu::K_COUNT; ++k) {
+            if (!smgpu::so_kid(k)) continue;
             const size_t smem = smgpu::so_kernel_smem(k);
             if (cudaFuncSetAttribute(na_kernel(k), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      static_cast<int>(smem)) != cudaSuccess)

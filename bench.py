@@ -1119,6 +1119,12 @@ def main():
             # The single-pattern bandwidth scans and the serving loop, in
             # compact form, so one default run reports every half of the
             # metric (each also runs alone: --workload bandwidth / serve).
+            # The sweep leaves tens of thousands of Python objects behind;
+            # freezing them keeps the garbage collector's full passes (which
+            # stop the serving scheduler thread) short.
+            import gc
+            gc.collect()
+            gc.freeze()
             out["bandwidth"] = bandwidth_record(args, local, compact=True)
             # The committed tuning table is measured on the sweep's 4 MiB
             # texts; the server's 2 GiB corpora run with the built-in rule,

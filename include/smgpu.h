@@ -103,7 +103,7 @@ typedef struct {
     uint32_t hist;        /* 1 if the Shift-Or state carries 16 match flags */
     uint32_t tile_starts; /* start positions per work item */
     uint64_t device_bytes;/* size of the plan's device tables */
-    uint32_t kernel;      /* internal kernel id (0..10): batches run one launch per id */
+    uint32_t kernel;      /* internal kernel id (0..11): batches run one launch per id */
     uint32_t reserved;
 } sm_plan_desc;
 

@@ -924,7 +924,7 @@ bool ticket_map(const std::vector<const uint8_t *> &text, const std::vector<uint
 // 16-byte chunks that hold one).  For skewed texts the hint should be an
 // effective alphabet size (see the Python package's hints module).
 bool packable(const sm_plan *p) {
-    if (p->kid != K_SO6P && p->kid != K_SO8H && p->kid != K_SO16H) return false;
+    if (p->kid != K_SO4Q && p->kid != K_SO6P && p->kid != K_SO8H && p->kid != K_SO16H) return false;
     if (p->sigma < 2) return false;
     return static_cast<double>(p->hdr.m) * std::log2(static_cast<double>(p->sigma)) >= 16.0;
 }

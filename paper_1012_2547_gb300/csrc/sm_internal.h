@@ -24,26 +24,27 @@ enum KernelId : int {
     K_LINEAR = 7, // per-segment Knuth-Morris-Pratt
     K_SOMULTI = 8, // several Shift-And patterns (m <= 16) of one text in one state (batches only)
     K_DFA = 9,     // per-segment string-matching automaton, table in shared memory
-    K_SO6P = 10,   // 32-bit state, byte masks, two text bytes per step, m <= 6
-    K_COUNT = 11
+    K_SO6P = 10,   // 32-bit state, byte masks, two text bytes per step, m = 5..6 (m <= 6 by id)
+    K_SO4Q = 11,   // 32-bit state, byte masks, four text bytes per step, m <= 4
+    K_COUNT = 12
 };
 
 // The bit-parallel kernels (staged sub-tiles, one-warp blocks).  Patterns
-// of m <= 6 and 7..8 have kernels of their own (two-byte and one-byte
-// steps), so a launch holds one scan loop's code, not both.
-inline bool so_kid(int kid) { return kid <= K_SO64A || kid == K_SO6P; }
+// of m <= 4, 5..6 and 7..8 have kernels of their own (four-, two- and
+// one-byte steps), so a launch holds one scan loop's code, not several.
+inline bool so_kid(int kid) { return kid <= K_SO64A || kid == K_SO6P || kid == K_SO4Q; }
 // Kernels that stage sub-tiles and use the per-block spill area.
 inline bool staged_kid(int kid) { return so_kid(kid) || kid == K_SOMULTI; }
 inline uint32_t so_entry_bytes(int kid) {
-    return kid == K_SO8H || kid == K_SO6P ? 1u : kid == K_SO16H ? 2u : (kid <= K_SO32A ? 4u : 8u);
+    return kid == K_SO8H || kid == K_SO6P || kid == K_SO4Q ? 1u : kid == K_SO16H ? 2u : (kid <= K_SO32A ? 4u : 8u);
 }
-inline uint32_t so_word_bits(int kid) { return kid <= K_SO32A || kid == K_SO6P ? 32u : 64u; }
+inline uint32_t so_word_bits(int kid) { return kid <= K_SO32A || kid == K_SO6P || kid == K_SO4Q ? 32u : 64u; }
 inline bool so_hist(int kid) { return kid != K_SO32A && kid != K_SO64A; }
 // Bit-parallel kernel for length m and state width wb (0 = choose), or -1.
 inline int so_kid_for(uint32_t m, uint32_t wb) {
     if (wb == 0) wb = m <= 32 ? 32u : 64u;
     if (wb == 32)
-        return m <= 6 ? K_SO6P : m <= 8 ? K_SO8H : m <= 16 ? K_SO16H : m <= 17 ? K_SO32H : m <= 32 ? K_SO32A : -1;
+        return m <= 4 ? K_SO4Q : m <= 6 ? K_SO6P : m <= 8 ? K_SO8H : m <= 16 ? K_SO16H : m <= 17 ? K_SO32H : m <= 32 ? K_SO32A : -1;
     if (wb == 64) return m <= 49 ? K_SO64H : m <= 64 ? K_SO64A : -1;
     return -1;
 }

@@ -116,11 +116,14 @@ __device__ __forceinline__ uint32_t lds_s8(uint32_t addr) {
 // Run-time constants of the scan steps: values the compiler cannot fold, so
 // that the state's shift stays an IMAD on the FMA pipe.
 struct SOK {
-    uint32_t tb;    // shared address of the mask table (256-aligned)
-    uint32_t tb1;   // pair step: shared address of the shifted-mask table (256-aligned)
-    uint32_t two;   // 2
-    uint32_t four;  // 4
-    uint32_t esz;   // bytes per table entry
+    uint32_t tb;       // shared address of the mask table B (256-aligned)
+    uint32_t tb1;      // multi-byte steps: shifted-mask tables B1, B2, B3
+    uint32_t tb2;      //   (B_k[c] = (B[c] << k) | (2^k - 1)), 256-aligned
+    uint32_t tb3;
+    uint32_t two;      // 2
+    uint32_t four;     // 4
+    uint32_t sixteen;  // 16
+    uint32_t esz;      // bytes per table entry
 };
 
 // Table entry of byte b of word x, widened to the state (zero above the
@@ -159,17 +162,28 @@ __device__ __forceinline__ Word so_update(Word D, Word e, uint32_t two) {
     return (D2 & e) | (K & (D2 | e));
 }
 
-// Four steps on the bytes of x.  PAIR (byte tables, m <= 6, 32-bit state):
-// two bytes per step.  Composing two steps,
-//   D <- ((D << 2) | 3) & B1[c1] & B[c2],   B1[c] = (B[c] << 1) | 1,
-// where both tables hold one byte per entry with every bit >= m of B (and
-// >= m+1 of B1) set; for m <= 6 bit 7 of both is set, so a sign-extending
-// load supplies the ones above the byte and one 3-input AND finishes the
-// step: per two bytes two PRMT, two loads, one IMAD and one LOP3 instead of
-// twice four instructions.
-template <typename Word, typename Entry, bool PAIR>
+// Four steps on the bytes of x, STEP text bytes per state update (byte
+// tables and a 32-bit state for STEP > 1).  Composing k single steps gives
+//   D <- ((D << k) | (2^k - 1)) & B_{k-1}[c_1] & ... & B_1[c_{k-1}] & B[c_k],
+//   B_j[c] = (B[c] << j) | (2^j - 1),
+// where each table holds one byte per entry with every bit >= m of B (so
+// >= m + j of B_j) set.  While m + STEP - 1 <= 7, bit 7 of every table
+// byte is set, so a sign-extending load supplies the ones above the byte:
+//   STEP 2 (m <= 6): per two bytes two PRMT, two loads, one IMAD, one LOP3;
+//   STEP 4 (m <= 4): per four bytes four PRMT, four loads, one IMAD and two
+//     LOP3, and the chain through D is one IMAD and one LOP3 per four bytes
+//     (the tables' AND is off the chain).
+template <typename Word, typename Entry, int STEP>
 __device__ __forceinline__ void so_step4(Word &D, uint32_t x, const SOK &k) {
-    if constexpr (PAIR) {
+    if constexpr (STEP == 4) {
+        static_assert(sizeof(Word) == 4 && sizeof(Entry) == 1, "quad steps use byte tables and a 32-bit state");
+        const uint32_t e3 = lds_s8(__byte_perm(x, k.tb3, 0x7650u));
+        const uint32_t e2 = lds_s8(__byte_perm(x, k.tb2, 0x7651u));
+        const uint32_t e1 = lds_s8(__byte_perm(x, k.tb1, 0x7652u));
+        const uint32_t e0 = lds_s8(__byte_perm(x, k.tb, 0x7653u));
+        const uint32_t t = e3 & e2 & e1;
+        D = (static_cast<uint32_t>(D) * k.sixteen + 15u) & t & e0;
+    } else if constexpr (STEP == 2) {
         static_assert(sizeof(Word) == 4 && sizeof(Entry) == 1, "pair steps use byte tables and a 32-bit state");
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -210,17 +224,17 @@ __device__ __forceinline__ uint32_t range_mask16(int cb, int elo, int ehi) {
 // Local scan of one lane segment from the empty state.  F[c] bit r flags an
 // occurrence ending at segment byte 16c + 15 - r; returns the final state,
 // which is exact because the segment is at least m bytes long.
-template <typename Word, typename Entry, bool HIST, bool PAIR>
+template <typename Word, typename Entry, bool HIST, int STEP>
 __device__ __forceinline__ Word so_local(const uint8_t *seg, Word D, const SOK &k, uint32_t m,
                                          uint32_t (&F)[SO_SEGC]) {
 #pragma unroll
     for (int c = 0; c < SO_SEGC; ++c) {
         const uint4 w = *reinterpret_cast<const uint4 *>(seg + 16 * c);
         if (HIST) {
-            so_step4<Word, Entry, PAIR>(D, w.x, k);
-            so_step4<Word, Entry, PAIR>(D, w.y, k);
-            so_step4<Word, Entry, PAIR>(D, w.z, k);
-            so_step4<Word, Entry, PAIR>(D, w.w, k);
+            so_step4<Word, Entry, STEP>(D, w.x, k);
+            so_step4<Word, Entry, STEP>(D, w.y, k);
+            so_step4<Word, Entry, STEP>(D, w.z, k);
+            so_step4<Word, Entry, STEP>(D, w.w, k);
             F[c] = static_cast<uint32_t>(D >> (m - 1)) & 0xFFFFu;
         } else {
             const Word Ds = D;
@@ -245,19 +259,19 @@ __device__ __forceinline__ Word so_local(const uint8_t *seg, Word D, const SOK &
 // State at the segment start from the WARM (8 or 16) bytes before it, run
 // from the empty state: exact for every bit below WARM, hence for all bits
 // that matter when m - 1 <= WARM.  Replaces the fix-up for short patterns.
-template <typename Word, typename Entry, int WARM, bool PAIR>
+template <typename Word, typename Entry, int WARM, int STEP>
 __device__ __forceinline__ Word so_warmup(const uint8_t *seg, const SOK &k) {
     Word D = 0;
     if (WARM == 8) {
         const uint2 w = *reinterpret_cast<const uint2 *>(seg - 8);
-        so_step4<Word, Entry, PAIR>(D, w.x, k);
-        so_step4<Word, Entry, PAIR>(D, w.y, k);
+        so_step4<Word, Entry, STEP>(D, w.x, k);
+        so_step4<Word, Entry, STEP>(D, w.y, k);
     } else if (WARM == 16) {
         const uint4 w = *reinterpret_cast<const uint4 *>(seg - 16);
-        so_step4<Word, Entry, PAIR>(D, w.x, k);
-        so_step4<Word, Entry, PAIR>(D, w.y, k);
-        so_step4<Word, Entry, PAIR>(D, w.z, k);
-        so_step4<Word, Entry, PAIR>(D, w.w, k);
+        so_step4<Word, Entry, STEP>(D, w.x, k);
+        so_step4<Word, Entry, STEP>(D, w.y, k);
+        so_step4<Word, Entry, STEP>(D, w.z, k);
+        so_step4<Word, Entry, STEP>(D, w.w, k);
     }
     return D;
 }
@@ -360,9 +374,9 @@ struct SOItem {
 };
 
 // Loads plan P's mask table into shared memory unless it is there already.
-// Byte tables also get the pair-step table B1[c] = (B[c] << 1) | 1 at
-// tbl + 256.
-template <typename Entry>
+// Byte tables also get NSHIFTED shifted tables B_j[c] = (B[c] << j) |
+// (2^j - 1), j = 1..NSHIFTED, at tbl + 256 j.
+template <typename Entry, int NSHIFTED>
 __device__ __forceinline__ void so_table(const PlanDev *P, const PlanDev *&cur_plan, uint8_t *tbl,
                                          uint32_t &m) {
     if (P == cur_plan) return;
@@ -373,13 +387,16 @@ __device__ __forceinline__ void so_table(const PlanDev *P, const PlanDev *&cur_p
     for (int c = lane; c < static_cast<int>(256 * sizeof(Entry) / 16); c += 32) {
         const uint4 v = __ldg(&src[c]);
         reinterpret_cast<uint4 *>(tbl)[c] = v;
-        if (sizeof(Entry) == 1) {
-            // Per byte (b << 1) | 1 within each 32-bit word: shift the word,
-            // drop the bits carried across bytes, set every byte's bit 0.
-            const uint32_t K = 0x01010101u, HI = 0xFEFEFEFEu;
-            reinterpret_cast<uint4 *>(tbl + 256)[c] =
-                make_uint4(((v.x << 1) & HI) | K, ((v.y << 1) & HI) | K, ((v.z << 1) & HI) | K,
-                           ((v.w << 1) & HI) | K);
+#pragma unroll
+        for (int j = 1; j <= NSHIFTED; ++j) {
+            // Per byte (b << j) | (2^j - 1) within each 32-bit word: shift
+            // the word, drop the bits carried across bytes, set every byte's
+            // low j bits.
+            const uint32_t K = 0x01010101u * ((1u << j) - 1u);
+            const uint32_t HI = 0x01010101u * ((0xFFu << j) & 0xFFu);
+            reinterpret_cast<uint4 *>(tbl + 256 * j)[c] =
+                make_uint4(((v.x << j) & HI) | K, ((v.y << j) & HI) | K, ((v.z << j) & HI) | K,
+                           ((v.w << j) & HI) | K);
         }
     }
     cur_plan = P;
@@ -390,17 +407,17 @@ __device__ __forceinline__ void so_table(const PlanDev *P, const PlanDev *&cur_p
 // Scan of one sub-tile staged at `buf` (its 64 preceding bytes included):
 // flags of the lane's segment, masked to the valid ends.  `carry` is the
 // exact state before the sub-tile (fix-up form only).
-template <typename Word, typename Entry, bool HIST, int WARM, bool PAIR>
+template <typename Word, typename Entry, bool HIST, int WARM, int STEP>
 __device__ __forceinline__ uint32_t so_subtile(const uint8_t *buf, const SOK &k, uint32_t m, Word &carry,
                                                bool warm_carry, int elo, int ehi,
                                                uint32_t (&F)[SO_SEGC]) {
     const int lane = threadIdx.x & 31;
     const uint8_t *seg = buf + lane * SO_S;
     if (WARM) {
-        so_local<Word, Entry, HIST, PAIR>(seg, so_warmup<Word, Entry, WARM, PAIR>(seg, k), k, m, F);
+        so_local<Word, Entry, HIST, STEP>(seg, so_warmup<Word, Entry, WARM, STEP>(seg, k), k, m, F);
     } else {
         if (warm_carry && lane == 0) carry = so_warm<Word, Entry>(buf - (m - 1), k.tb, m, k.esz);
-        const Word Dend = so_local<Word, Entry, HIST, false>(seg, Word(0), k, m, F);
+        const Word Dend = so_local<Word, Entry, HIST, 1>(seg, Word(0), k, m, F);
         Word Dprev = __shfl_up_sync(0xffffffffu, Dend, 1);
         if (lane == 0) Dprev = carry;
         so_fixup<Word, Entry>(seg, k.tb, m, k.esz, Dprev, F);
@@ -460,14 +477,17 @@ __device__ __forceinline__ void so_write_flags(const uint32_t (&F)[SO_SEGC], uin
 // copied out.  Two hit buffers and two spill areas alternate between the
 // item being scanned and the item waiting for its prefix.  Without a spill
 // area an item whose hits overflow the buffer is rescanned at write time.
-template <typename Word, typename Entry, bool HIST, int WARM, bool PAIR = false>
+template <typename Word, typename Entry, bool HIST, int WARM, int STEP = 1>
 __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchArgs a) {
     using L = SOLayout<Entry>;
-    static_assert(!PAIR || (sizeof(Word) == 4 && sizeof(Entry) == 1 && HIST && WARM != 0),
-                  "two-byte steps need byte tables, a 32-bit state and the warm-up form");
-    constexpr bool PAIR_OK = PAIR;
+    static_assert(STEP == 1 || STEP == 2 || STEP == 4, "one, two or four text bytes per step");
+    static_assert(STEP == 1 || (sizeof(Word) == 4 && sizeof(Entry) == 1 && HIST && WARM != 0),
+                  "multi-byte steps need byte tables, a 32-bit state and the warm-up form");
+    // Byte tables: B, then the shifted tables the steps use (B1 for STEP 1
+    // and 2; B1, B2, B3 for STEP 4).
+    constexpr int NSHIFTED = sizeof(Entry) != 1 ? 0 : STEP == 4 ? 3 : 1;
     extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ __align__(256) uint8_t tbl[256 * sizeof(Entry) + (sizeof(Entry) == 1 ? 256 : 0)];
+    __shared__ __align__(256) uint8_t tbl[256 * sizeof(Entry) + 256 * NSHIFTED];
     const uint32_t tb = smem_addr(tbl);
     uint32_t *hits_base = reinterpret_cast<uint32_t *>(smem + L::HITS_OFF);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L::BAR_OFF);
@@ -483,6 +503,7 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
         consts[0] = 2u;
         consts[1] = static_cast<uint32_t>(sizeof(Entry));
         consts[2] = 4u;
+        consts[3] = 16u;
         for (int b = 0; b < SO_NBUF; ++b) mbar_init(&bar[b], 1);
         fence_mbar_init();
         if (so_claim(a, &t, &qi, &k)) {
@@ -499,7 +520,7 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
     t = __shfl_sync(0xffffffffu, t, 0);
     qi = __shfl_sync(0xffffffffu, qi, 0);
     k = __shfl_sync(0xffffffffu, k, 0);
-    const SOK kk{tb, tb + 256u, consts[0], consts[2], consts[1]};
+    const SOK kk{tb, tb + 256u, tb + 512u, tb + 768u, consts[0], consts[2], consts[3], consts[1]};
 
     const PlanDev *cur_plan = nullptr;
     uint32_t m = 1;
@@ -609,8 +630,7 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
         // Too many hits to buffer and no spill area: rescan the item in the
         // ring slot that no prefetch uses, writing each sub-tile's hits at
         // their final offsets.
-        so_table<Entry>(Q.plan, cur_plan, tbl, m);
-        constexpr bool pair = PAIR_OK;
+        so_table<Entry, NSHIFTED>(Q.plan, cur_plan, tbl, m);
         const uint64_t qn = Q.n;
         const int64_t vlo = o + static_cast<int64_t>(m) - 1;
         const int64_t vhi = o + static_cast<int64_t>(qn);
@@ -631,9 +651,7 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
             uint32_t F[SO_SEGC];
             const uint8_t *buf = smem + wb * SO_BUF + SO_LHALO;
             const bool first = s == pend.sb && s > 0;
-            const uint32_t cnt =
-                pair ? so_subtile<Word, Entry, HIST, WARM, PAIR_OK>(buf, kk, m, carry, first, elo, ehi, F)
-                     : so_subtile<Word, Entry, HIST, WARM, false>(buf, kk, m, carry, first, elo, ehi, F);
+            const uint32_t cnt = so_subtile<Word, Entry, HIST, WARM, STEP>(buf, kk, m, carry, first, elo, ehi, F);
             uint32_t total;
             const uint32_t ex = warp_excl_scan(cnt, &total);
             so_write_flags(F, ex, run, cap, out, static_cast<int64_t>(s) * SO_T - shift);
@@ -644,8 +662,7 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
 
     while (t < a.total) {
         const QueryDev &Q = query_of(a, qi);
-        so_table<Entry>(Q.plan, cur_plan, tbl, m);
-        constexpr bool pair = PAIR_OK;  // two bytes per step (see so_step4); the plan's m <= 6
+        so_table<Entry, NSHIFTED>(Q.plan, cur_plan, tbl, m);
         // Query fields in registers: the mbarrier waits are compiler
         // barriers, after which descriptor fields would be reloaded.
         const uint8_t *const qtext = Q.text;
@@ -691,9 +708,7 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
             uint32_t F[SO_SEGC];
             const uint8_t *buf = smem + cur * SO_BUF + SO_LHALO;
             const bool first = s == sb && s > 0;
-            const uint32_t cnt =
-                pair ? so_subtile<Word, Entry, HIST, WARM, PAIR_OK>(buf, kk, m, carry, first, elo, ehi, F)
-                     : so_subtile<Word, Entry, HIST, WARM, false>(buf, kk, m, carry, first, elo, ehi, F);
+            const uint32_t cnt = so_subtile<Word, Entry, HIST, WARM, STEP>(buf, kk, m, carry, first, elo, ehi, F);
             uint32_t total = 0, ex = 0;
             if (__any_sync(0xffffffffu, cnt != 0)) ex = warp_excl_scan(cnt, &total);
             if (total != 0 && spill) {
@@ -1212,7 +1227,8 @@ __global__ void __launch_bounds__(32) mp_kernel(const __grid_constant__ LaunchAr
 
 const void *so_kernel_fn(int kid) {
     switch (kid) {
-        case K_SO6P: return reinterpret_cast<const void *>(&so_kernel<uint32_t, uint8_t, true, 8, true>);
+        case K_SO4Q: return reinterpret_cast<const void *>(&so_kernel<uint32_t, uint8_t, true, 8, 4>);
+        case K_SO6P: return reinterpret_cast<const void *>(&so_kernel<uint32_t, uint8_t, true, 8, 2>);
         case K_SO8H: return reinterpret_cast<const void *>(&so_kernel<uint32_t, uint8_t, true, 8>);
         case K_SO16H: return reinterpret_cast<const void *>(&so_kernel<uint32_t, uint16_t, true, 16>);
         case K_SO32H: return reinterpret_cast<const void *>(&so_kernel<uint32_t, uint32_t, true, 16>);

@@ -427,19 +427,38 @@ __device__ __forceinline__ uint32_t so_subtile(const uint8_t *buf, const SOK &k,
 }
 
 // Calls put(b) for every flagged byte b of a lane segment, b increasing.
-// F[c] bit r flags byte 16c + 15 - r.  The flags are taken 32 bytes at a
-// time in byte order (two chunks' flags bit-reversed side by side), one
-// loop per word with 32-bit operations, one iteration per hit.
+// F[c] bit r flags byte 16c + 15 - r; one loop per 32 bytes, one iteration
+// per hit.  Two forms (both exact; which one compiles better depends on
+// the kernel around it, so each kernel takes the one measured faster):
+//   MSB_FIRST: g = F[2w] << 16 | F[2w+1] (one PRMT) flags byte 32w + 31 - p
+//     at bit p, so taking the highest set bit first (BFIND) yields the
+//     bytes in increasing order without bit-reversing the flags;
+//   otherwise: the two chunks' flags bit-reversed side by side, lowest set
+//     bit first.
 static_assert(SO_SEGC == 9, "so_emit packs 9 chunks of flags");
-template <typename Put>
+__device__ __forceinline__ uint32_t bfind_u32(uint32_t x) {
+    uint32_t p;
+    asm("bfind.u32 %0, %1;" : "=r"(p) : "r"(x));
+    return p;
+}
+template <bool MSB_FIRST, typename Put>
 __device__ __forceinline__ void so_emit(const uint32_t (&F)[SO_SEGC], Put put) {
 #pragma unroll
     for (int w = 0; w < 5; ++w) {
-        uint32_t q = (__brev(F[2 * w]) >> 16) | (2 * w + 1 < SO_SEGC ? __brev(F[2 * w + 1]) : 0u);
-        while (q) {
-            const uint32_t b = static_cast<uint32_t>(__ffs(q)) - 1u;
-            q &= q - 1u;
-            put(32u * w + b);
+        if constexpr (MSB_FIRST) {
+            uint32_t g = 2 * w + 1 < SO_SEGC ? __byte_perm(F[2 * w + 1], F[2 * w], 0x5410u) : F[2 * w] << 16;
+            while (g) {
+                const uint32_t p = bfind_u32(g);
+                g ^= 1u << p;
+                put(32u * w + 31u - p);
+            }
+        } else {
+            uint32_t q = (__brev(F[2 * w]) >> 16) | (2 * w + 1 < SO_SEGC ? __brev(F[2 * w + 1]) : 0u);
+            while (q) {
+                const uint32_t b = static_cast<uint32_t>(__ffs(q)) - 1u;
+                q &= q - 1u;
+                put(32u * w + b);
+            }
         }
     }
 }
@@ -447,6 +466,7 @@ __device__ __forceinline__ void so_emit(const uint32_t (&F)[SO_SEGC], Put put) {
 // Writes the flagged positions of a lane segment at out[idx...] (capped):
 // idx0 + ex is the lane's first index, start0 the output value of sub-tile
 // position 0.
+template <bool MSB_FIRST>
 __device__ __forceinline__ void so_write_flags(const uint32_t (&F)[SO_SEGC], uint32_t ex, uint64_t idx0,
                                                uint64_t cap, uint64_t *out, int64_t start0) {
     const uint64_t first = idx0 + ex;
@@ -457,7 +477,7 @@ __device__ __forceinline__ void so_write_flags(const uint32_t (&F)[SO_SEGC], uin
     uint64_t *dst = out + first;
     const int64_t lane0 = start0 + static_cast<int64_t>(threadIdx.x & 31) * SO_S;
     uint32_t j = 0;
-    so_emit(F, [&](uint32_t b) {
+    so_emit<MSB_FIRST>(F, [&](uint32_t b) {
         if (j < room) dst[j] = static_cast<uint64_t>(lane0 + b);
         ++j;
     });
@@ -486,6 +506,7 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
     // Byte tables: B, then the shifted tables the steps use (B1 for STEP 1
     // and 2; B1, B2, B3 for STEP 4).
     constexpr int NSHIFTED = sizeof(Entry) != 1 ? 0 : STEP == 4 ? 3 : 1;
+    constexpr bool EMIT_MSB = STEP > 1;  // so_emit form (measured per kernel)
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(256) uint8_t tbl[256 * sizeof(Entry) + 256 * NSHIFTED];
     const uint32_t tb = smem_addr(tbl);
@@ -615,7 +636,7 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
                     if (!split || half == h) {
                         uint16_t *d = stage + (ex - lo);
                         const uint32_t r0 = static_cast<uint32_t>(lane) * SO_S;
-                        so_emit(F, [&](uint32_t b) { *d++ = static_cast<uint16_t>(r0 + b); });
+                        so_emit<EMIT_MSB>(F, [&](uint32_t b) { *d++ = static_cast<uint16_t>(r0 + b); });
                     }
                     __syncwarp();
                     const uint64_t at = run + lo;
@@ -654,7 +675,7 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
             const uint32_t cnt = so_subtile<Word, Entry, HIST, WARM, STEP>(buf, kk, m, carry, first, elo, ehi, F);
             uint32_t total;
             const uint32_t ex = warp_excl_scan(cnt, &total);
-            so_write_flags(F, ex, run, cap, out, static_cast<int64_t>(s) * SO_T - shift);
+            so_write_flags<EMIT_MSB>(F, ex, run, cap, out, static_cast<int64_t>(s) * SO_T - shift);
             run += total;
             __syncwarp();
         }
@@ -732,7 +753,7 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
             } else if (cnt && (mode == 1 || count + total <= SO_HITS)) {
                 uint32_t *dst = mode == 0 ? hits + count + ex : list + (count - buffered) + ex;
                 const uint32_t rel0 = static_cast<uint32_t>(x - ivstart);
-                so_emit(F, [&](uint32_t b) { *dst++ = rel0 + b; });
+                so_emit<EMIT_MSB>(F, [&](uint32_t b) { *dst++ = rel0 + b; });
             }
             count += total;
             __syncwarp();  // slot `cur` and the hit buffer are settled
@@ -1084,7 +1105,7 @@ __global__ void __launch_bounds__(32) mp_kernel(const __grid_constant__ LaunchAr
                 const uint32_t c = so_mask_count(F, elo, ehi);
                 uint32_t total;
                 const uint32_t exl = warp_excl_scan(c, &total);
-                so_write_flags(F, exl, run, cp, op, static_cast<int64_t>(s) * SO_T - sh);
+                so_write_flags<false>(F, exl, run, cp, op, static_cast<int64_t>(s) * SO_T - sh);
                 run += total;
             }
         }

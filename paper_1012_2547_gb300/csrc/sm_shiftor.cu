@@ -641,21 +641,24 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
                     __syncwarp();
                     const uint64_t at = run + lo;
                     const uint32_t nw = at >= cap ? 0u : cap - at < cnt_h ? static_cast<uint32_t>(cap - at) : cnt_h;
-                    // Four stage loads per lane ahead of their four stores
-                    // (the multi-byte-step kernels, which the dense short
-                    // patterns use; the one-byte-step kernels keep the plain
-                    // loop, which needs fewer registers there).
-                    uint64_t *o = out + at;
-                    uint32_t i = lane;
-                    if constexpr (EMIT_MSB)
-                    for (; i + 96 < nw; i += 128) {
-                        const uint32_t v0 = stage[i], v1 = stage[i + 32], v2 = stage[i + 64], v3 = stage[i + 96];
-                        o[i] = static_cast<uint64_t>(base + v0);
-                        o[i + 32] = static_cast<uint64_t>(base + v1);
-                        o[i + 64] = static_cast<uint64_t>(base + v2);
-                        o[i + 96] = static_cast<uint64_t>(base + v3);
+                    if constexpr (EMIT_MSB) {
+                        // Four stage loads per lane ahead of their four
+                        // stores (the multi-byte-step kernels, which the
+                        // dense short patterns use).
+                        uint64_t *dst = out + at;
+                        uint32_t i = lane;
+                        for (; i + 96 < nw; i += 128) {
+                            const uint32_t v0 = stage[i], v1 = stage[i + 32], v2 = stage[i + 64],
+                                           v3 = stage[i + 96];
+                            dst[i] = static_cast<uint64_t>(base + v0);
+                            dst[i + 32] = static_cast<uint64_t>(base + v1);
+                            dst[i + 64] = static_cast<uint64_t>(base + v2);
+                            dst[i + 96] = static_cast<uint64_t>(base + v3);
+                        }
+                        for (; i < nw; i += 32) dst[i] = static_cast<uint64_t>(base + stage[i]);
+                    } else {
+                        for (uint32_t i = lane; i < nw; i += 32) out[at + i] = static_cast<uint64_t>(base + stage[i]);
                     }
-                    for (; i < nw; i += 32) o[i] = static_cast<uint64_t>(base + stage[i]);
                     __syncwarp();
                 }
                 run += total;

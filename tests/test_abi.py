@@ -69,6 +69,10 @@ def test_host_argument_checks(lib):
     assert lib.sm_search_batch(None, 0, None) == _lib.SM_OK
     assert lib.sm_plan_free(None) == _lib.SM_OK
     assert lib.sm_batch_free(None) == _lib.SM_OK
+    assert lib.sm_plan_free_many(None, 0) == _lib.SM_OK
+    assert lib.sm_plan_free_many(None, 3) == _lib.SM_EINVAL
+    nulls = (ctypes.c_void_p * 3)()
+    assert lib.sm_plan_free_many(nulls, 3) == _lib.SM_OK  # null entries are skipped
 
 
 def test_noalloc_host_checks(lib):

@@ -450,9 +450,9 @@ class Server:
                     texts.append(self.corpora[r.corpus])
             t1 = time.perf_counter()
             hint = self.sigma_hints.get(batch[0].corpus, self.own_text_sigma)
-            # Plans upload on a stream of their own: prepare_many waits for
+            # Plans upload on a stream of their own: the prepare call waits for
             # its stream, which must not hold this batch's text uploads.
-            plans = smg.prepare_many([r.pattern for r in batch], sigma_hint=hint, stream=self._prep_stream)
+            plans = smg.prepare_array([r.pattern for r in batch], sigma_hint=hint, stream=self._prep_stream)
             t2 = time.perf_counter()
             caps = np.array([r.cap for r in batch], dtype=np.int64)
             offs = np.concatenate([[0], np.cumsum(caps)])
@@ -592,8 +592,7 @@ class Server:
             # policy's rate estimates; plans and memory are released.
             scan_s = rec["ev0"].elapsed_time(rec["ev_c"]) / 1e3
             copy_s = rec["ev_c"].elapsed_time(rec["event"]) / 1e3
-            for p in rec["keep"][1]:
-                p.free()
+            rec["keep"][1].free()
             with self._lock:
                 self.policy.observe(rec["scan"], scan_s, rec["out_bytes"], copy_s)
                 self.policy.release(rec["reserved"])

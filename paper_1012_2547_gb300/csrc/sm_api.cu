@@ -461,7 +461,13 @@ sm_status build_blob(const uint8_t *p, uint32_t m, uint32_t sigma, const sm_conf
         uint64_t B[256];
         for (int c = 0; c < 256; ++c) B[c] = ~low;
         for (uint32_t j = 0; j < m; ++j) B[p[j]] |= 1ull << j;
-        for (int c = 0; c < 256; ++c) std::memcpy(b + h.off_tbl + esz * c, &B[c], esz);
+        uint8_t *tb = b + h.off_tbl;
+        switch (esz) {  // typed stores: the low esz bytes, little-endian as the device reads them
+            case 1: for (int c = 0; c < 256; ++c) tb[c] = static_cast<uint8_t>(B[c]); break;
+            case 2: for (int c = 0; c < 256; ++c) reinterpret_cast<uint16_t *>(tb)[c] = static_cast<uint16_t>(B[c]); break;
+            case 4: for (int c = 0; c < 256; ++c) reinterpret_cast<uint32_t *>(tb)[c] = static_cast<uint32_t>(B[c]); break;
+            default: for (int c = 0; c < 256; ++c) reinterpret_cast<uint64_t *>(tb)[c] = B[c]; break;
+        }
     }
     std::memcpy(b + h.off_pat, p, m);
     if (h.variant == VAR_QGRAM) {
@@ -487,9 +493,9 @@ sm_status build_blob(const uint8_t *p, uint32_t m, uint32_t sigma, const sm_conf
         }
         // Bitmap bit of every key: top bm_bits bits of the two 32-bit
         // halves' multiplicative hashes xored (the same function as the
-        // kernel's probe loop).
-        thread_local std::vector<uint32_t> fill;
-        fill.assign(size_t(mask) + 1, 0);
+        // kernel's probe loop).  `first` is first set one past each run,
+        // then moved down as the run is filled with j ascending, so the run
+        // holds j descending and `first` ends at the run's start.
         uint32_t run = 0;
         for (uint32_t sl = 0; sl <= mask; ++sl) {
             if (slots[sl].count) {
@@ -499,13 +505,10 @@ sm_status build_blob(const uint8_t *p, uint32_t m, uint32_t sigma, const sm_conf
                 const uint32_t bb = h32 >> (32 - h.bm_bits);
                 bitmap[bb >> 5] |= 1u << (bb & 31);
             }
-            slots[sl].first = run;
             run += slots[sl].count;
+            slots[sl].first = run;
         }
-        for (uint32_t j = ng; j-- > 0;) {
-            const uint32_t sl = slot_of[j];
-            offs[slots[sl].first + fill[sl]++] = j;
-        }
+        for (uint32_t j = 0; j < ng; ++j) offs[--slots[slot_of[j]].first] = j;
     }
     std::memcpy(b + h.off_fail, fail.data(), 4ull * (m + 1));
     if (with_dfa) {

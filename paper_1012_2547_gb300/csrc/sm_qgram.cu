@@ -267,19 +267,6 @@ struct VSink {
     }
 };
 
-// Exclusive warp scan of v (whole warp); *total receives the warp's sum.
-__device__ __forceinline__ uint32_t qg_warp_scan(uint32_t v, uint32_t *total) {
-    const uint32_t lane = threadIdx.x & 31u;
-    uint32_t x = v;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
-        if (lane >= static_cast<uint32_t>(d)) x += y;
-    }
-    *total = __shfl_sync(0xffffffffu, x, 31);
-    return x - v;
-}
-
 // Filter state a warp carries across its probe rounds.
 struct QGRun {
     uint64_t ncand;  // candidates fully checked so far (density guard)

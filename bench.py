@@ -163,11 +163,11 @@ def source_hash(files=SHIFTAND_SOURCES) -> str:
     return h.hexdigest()[:16]
 
 
-def committed_profile(kernel: str) -> dict:
+def committed_profile(kernel: str, path: str | None = None) -> dict:
     """Per-launch ncu figures of `kernel` (dram bytes, thread instructions)
-    from profiles/traffic.txt, when they were taken on the current sources;
-    else {}."""
-    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    from profiles/traffic.txt (or `path`), when they were taken on the
+    current sources; else {}."""
+    path = path or os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return {}
     cur = source_hash()
@@ -241,6 +241,36 @@ def sweep_kwargs(args) -> dict:
     if args.per_m:
         kw["per_m"] = args.per_m
     return kw
+
+
+def roofline_record(alg_bytes: float, scanned: float, t: float, prof: dict, hbm: float, peak_kind: str,
+                    sms: int, mhz: float) -> dict:
+    """Roofline of the dominant family from its algorithmic bytes per launch,
+    its live launch time `t` (s) and its committed ncu figures `prof`
+    (bytes_per_launch = DRAM traffic, inst_per_launch = thread instructions;
+    either may be absent).  The family is L2-fed, and so bound by instruction
+    issue, when its DRAM traffic is under half its algorithmic bytes; then
+    `achieved` is thread instructions per second against the issue ceiling
+    (SMs x 4 schedulers x 32 lanes x the SM clock).  Otherwise it is HBM
+    bound: algorithmic bytes per second against the measured copy peak."""
+    traffic = prof.get("bytes_per_launch")
+    achieved = alg_bytes / t / 1e9
+    hbm_view = {"achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "peak_kind": peak_kind}
+    issue_peak = sms * 128 * mhz * 1e6 / 1e9  # G thread instructions / s
+    issue = {"peak": round(issue_peak, 1), "unit": "Ginst/s",
+             "peak_basis": f"{sms} SMs x 128 lanes x {mhz:.0f} MHz"}
+    if "inst_per_launch" in prof:
+        ach_i = prof["inst_per_launch"] / t / 1e9
+        issue.update({"achieved": round(ach_i, 1), "frac": round(ach_i / issue_peak, 4),
+                      "inst_per_scanned_byte": round(prof["inst_per_launch"] / scanned, 3),
+                      "inst_basis": "smsp__thread_inst_executed.sum per launch, committed ncu capture"})
+    l2_fed = traffic is not None and traffic < 0.5 * alg_bytes
+    if l2_fed and "achieved" in issue:
+        return {"bound": "alu", "achieved": issue["achieved"], "peak": issue["peak"], "unit": "Ginst/s",
+                "frac": issue["frac"], "traffic": traffic, "hbm_view": hbm_view}
+    return {"bound": "hbm", "achieved": hbm_view["achieved"], "peak": hbm, "unit": "GB/s",
+            "frac": hbm_view["frac"], "traffic": traffic, "issue": issue}
 
 
 KERNEL_NAMES = ["so_kernel<u32,u8,H>", "so_kernel<u32,u16,H>", "so_kernel<u32,u32,H>",
@@ -435,31 +465,9 @@ def run_ours(args, world, rank, local):
     dom_t = statistics.mean(dom["times"])
     kname = family_name(dom["key"])
     prof = committed_profile(kname + ":" + w.name)
-    traffic = prof.get("bytes_per_launch")
-    achieved = dom["alg_bytes"] / dom_t / 1e9
-    hbm_view = {"achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(achieved / hbm, 4), "peak_kind": peak_kind}
-    # Issue ceiling: SMs x 4 schedulers x 32 lanes x SM clock (thread
-    # instructions per second); the clock is the median sampled under load.
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = (clk or {}).get("sm_mhz") or SM_MAX_MHZ
-    issue_peak = sms * 128 * mhz * 1e6 / 1e9  # G thread instructions / s
-    issue = {"peak": round(issue_peak, 1), "unit": "Ginst/s",
-             "peak_basis": f"{sms} SMs x 128 lanes x {mhz:.0f} MHz"}
-    if "inst_per_launch" in prof:
-        ach_i = prof["inst_per_launch"] / dom_t / 1e9
-        issue.update({"achieved": round(ach_i, 1), "frac": round(ach_i / issue_peak, 4),
-                      "inst_per_scanned_byte": round(prof["inst_per_launch"] / dom["scanned"], 3),
-                      "inst_basis": "smsp__thread_inst_executed.sum per launch, committed ncu capture"})
-    # The family's texts stay in L2 across its searches when its DRAM traffic
-    # is well under its algorithmic bytes; then issue, not HBM, bounds it.
-    l2_fed = traffic is not None and traffic < 0.5 * dom["alg_bytes"]
-    if l2_fed and "achieved" in issue:
-        roofline = {"bound": "alu", "achieved": issue["achieved"], "peak": issue["peak"],
-                    "unit": "Ginst/s", "frac": issue["frac"], "traffic": traffic, "hbm_view": hbm_view}
-    else:
-        roofline = {"bound": "hbm", "achieved": hbm_view["achieved"], "peak": hbm, "unit": "GB/s",
-                    "frac": hbm_view["frac"], "traffic": traffic, "issue": issue}
+    roofline = roofline_record(dom["alg_bytes"], dom["scanned"], dom_t, prof, hbm, peak_kind, sms, mhz)
     roofline.update({
         "kernel": kname, "peak_kind": peak_kind, "alg_bytes_per_launch": dom["alg_bytes"],
         "kernel_ms": round(dom_t * 1e3, 4), "kernel_share": round(dom_t / per_step, 4),

@@ -62,12 +62,18 @@ constexpr int SO_NBUF = SO_NBUF_SLOTS;
 #endif
 constexpr int SO_HITS = SO_HIT_SLOTS;
 constexpr uint32_t SO_MAX_SUB = 64;         // most sub-tiles per work item
-constexpr uint32_t SO_SUB_FLAGS = SO_SEGC * 32 * 2;            // 16-bit flags of a sub-tile
+// A spilled sub-tile: per lane its flags as 5 words (two chunks each, see
+// so_flag_word) and its offset word (exclusive offset | hit count << 16),
+// word w of lane l at [w * 32 + l].
+constexpr uint32_t SO_SUB_WORDS = 6;
+constexpr uint32_t SO_SUB_FLAGS = SO_SUB_WORDS * 32 * 4;
 // Spill area of one item: a list of item-relative positions (4 bytes per
 // hit: cheaper than flag words below about one hit per 32 bytes), then the
 // flag words of the sub-tiles that follow once the list is full.
 constexpr uint32_t SO_SPILL_POS = 4096;
-constexpr uint32_t SO_SPILL_ITEM = SO_SPILL_POS * 4 + SO_MAX_SUB * SO_SUB_FLAGS;
+// (+256: with an item stride of exactly 64 KiB the packed kernel compiled
+// to 111 registers instead of 94.)
+constexpr uint32_t SO_SPILL_ITEM = SO_SPILL_POS * 4 + SO_MAX_SUB * SO_SUB_FLAGS + 256;
 constexpr uint32_t SO_SPILL_BYTES = 2 * SO_SPILL_ITEM;          // per block (two items)
 
 // Dynamic shared memory of a block: the staging ring, the item hit buffer,
@@ -463,6 +469,35 @@ __device__ __forceinline__ void so_emit(const uint32_t (&F)[SO_SEGC], Put put) {
     }
 }
 
+// Flag word w of a lane segment: chunks 2w and 2w + 1 side by side (bit p
+// flags byte 32w + 31 - p).
+__device__ __forceinline__ uint32_t so_flag_word(const uint32_t (&F)[SO_SEGC], int w) {
+    return 2 * w + 1 < SO_SEGC ? __byte_perm(F[2 * w + 1], F[2 * w], 0x5410u) : F[2 * w] << 16;
+}
+
+// so_emit over the 5 flag words of a segment (so_flag_word).
+template <bool MSB_FIRST, typename Put>
+__device__ __forceinline__ void so_emit_words(const uint32_t (&G)[5], Put put) {
+#pragma unroll
+    for (int w = 0; w < 5; ++w) {
+        if constexpr (MSB_FIRST) {
+            uint32_t g = G[w];
+            while (g) {
+                const uint32_t p = bfind_u32(g);
+                g ^= 1u << p;
+                put(32u * w + 31u - p);
+            }
+        } else {
+            uint32_t q = __brev(G[w]);
+            while (q) {
+                const uint32_t b = static_cast<uint32_t>(__ffs(q)) - 1u;
+                q &= q - 1u;
+                put(32u * w + b);
+            }
+        }
+    }
+}
+
 // Writes the flagged positions of a lane segment at out[idx...] (capped):
 // idx0 + ex is the lane's first index, start0 the output value of sub-tile
 // position 0.
@@ -605,25 +640,26 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
             // each).
             uint16_t *stage = reinterpret_cast<uint16_t *>(smem + (cur == 0 ? SO_NBUF - 1 : cur - 1) * SO_BUF);
             const uint32_t half = static_cast<uint32_t>(lane) >> 4;
-            // The next sub-tile's flags are loaded before this one's stores
-            // (software pipelining over the L2 latency).
-            uint32_t Fn[SO_SEGC];
-            const uint16_t *fsrc = reinterpret_cast<const uint16_t *>(flags) + lane;
+            // The next sub-tile's flag and offset words are loaded before
+            // this one's stores (software pipelining over the L2 latency);
+            // the offsets were taken by the scan, so no count or warp scan
+            // is redone here.
+            uint32_t Gn[SO_SUB_WORDS];
+            const uint32_t *fsrc = reinterpret_cast<const uint32_t *>(flags) + lane;
 #pragma unroll
-            for (int c = 0; c < SO_SEGC; ++c) Fn[c] = pend.flag_from < pend.se ? fsrc[c * 32] : 0u;
+            for (int w = 0; w < static_cast<int>(SO_SUB_WORDS); ++w)
+                Gn[w] = pend.flag_from < pend.se ? fsrc[w * 32] : 0u;
             for (uint64_t s = pend.flag_from; s < pend.se && run < cap; ++s) {
-                uint32_t F[SO_SEGC];
-                uint32_t cnt = 0;
+                uint32_t G[5];
                 const bool more = s + 1 < pend.se;
-                fsrc += SO_SUB_FLAGS / 2;
+                fsrc += SO_SUB_FLAGS / 4;
+                const uint32_t E = Gn[5];
 #pragma unroll
-                for (int c = 0; c < SO_SEGC; ++c) {
-                    F[c] = Fn[c];
-                    cnt += __popc(F[c]);
-                    Fn[c] = more ? fsrc[c * 32] : 0u;
-                }
-                uint32_t total;
-                const uint32_t ex = warp_excl_scan(cnt, &total);
+                for (int w = 0; w < 5; ++w) G[w] = Gn[w];
+#pragma unroll
+                for (int w = 0; w < static_cast<int>(SO_SUB_WORDS); ++w) Gn[w] = more ? fsrc[w * 32] : 0u;
+                const uint32_t ex = E & 0xFFFFu;
+                const uint32_t total = __shfl_sync(0xffffffffu, ex + (E >> 16), 31);
                 const bool split = total > SO_BUF / 2;
                 // First hit of pass 1: lanes 16..31 when split, else none.
                 const uint32_t lo1 = split ? __shfl_sync(0xffffffffu, ex, 16) : total;
@@ -636,7 +672,7 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
                     if (!split || half == h) {
                         uint16_t *d = stage + (ex - lo);
                         const uint32_t r0 = static_cast<uint32_t>(lane) * SO_S;
-                        so_emit<EMIT_MSB>(F, [&](uint32_t b) { *d++ = static_cast<uint16_t>(r0 + b); });
+                        so_emit_words<EMIT_MSB>(G, [&](uint32_t b) { *d++ = static_cast<uint16_t>(r0 + b); });
                     }
                     __syncwarp();
                     const uint64_t at = run + lo;
@@ -763,10 +799,12 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
                 }
             }
             if (mode == 2) {
-                // Keep this sub-tile's flags for the write phase.
-                uint16_t *dst = reinterpret_cast<uint16_t *>(flags + (s - flag_from) * SO_SUB_FLAGS);
+                // Keep this sub-tile's flag words and offsets for the write
+                // phase.
+                uint32_t *dst = reinterpret_cast<uint32_t *>(flags + (s - flag_from) * SO_SUB_FLAGS);
 #pragma unroll
-                for (int c = 0; c < SO_SEGC; ++c) dst[c * 32 + lane] = static_cast<uint16_t>(F[c]);
+                for (int w = 0; w < 5; ++w) dst[w * 32 + lane] = so_flag_word(F, w);
+                dst[5 * 32 + lane] = ex | (cnt << 16);
             } else if (cnt && (mode == 1 || count + total <= SO_HITS)) {
                 uint32_t *dst = mode == 0 ? hits + count + ex : list + (count - buffered) + ex;
                 const uint32_t rel0 = static_cast<uint32_t>(x - ivstart);
@@ -840,7 +878,8 @@ __global__ void __launch_bounds__(32) so_kernel(const __grid_constant__ LaunchAr
 // most 16 bits, so all fields are exact after it).
 
 constexpr int MP_REC = 4;  // (pattern, position) records a lane keeps in registers per sub-tile
-constexpr uint32_t MP_LIST = SO_SPILL_ITEM / 4;  // records of a work item (its whole spill area)
+constexpr uint32_t MP_LIST = 13312;  // records of a work item (52 KB of its spill area)
+static_assert(MP_LIST * 4 <= SO_SPILL_ITEM, "the records of an item fit its spill area");
 
 struct MPLayout {
     static constexpr uint32_t BAR_OFF = SO_NBUF * SO_BUF;

@@ -151,15 +151,24 @@ class ClockSampler:
 SHIFTAND_SOURCES = ("sm_common.cuh", "sm_internal.h", "sm_shiftor.cu")
 
 
+def _code_only(src: str) -> str:
+    """C++/CUDA source without comments and whitespace (string literals are
+    kept as they are), so that editing a comment leaves the hash alone."""
+    import re
+    tok = re.compile(r'"(?:\\.|[^"\\])*"|//[^\n]*|/\*.*?\*/|\s+', re.S)
+    return tok.sub(lambda m: m.group(0) if m.group(0).startswith('"') else "", src)
+
+
 def source_hash(files=SHIFTAND_SOURCES) -> str:
-    """Hash of the CUDA sources a kernel is compiled from (ties committed ncu
-    traffic to the build of that kernel)."""
+    """Hash of the code (comments and whitespace left out) of the CUDA
+    sources a kernel is compiled from: ties committed ncu traffic to the
+    build of that kernel."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1012_2547_gb300", "csrc")
     for f in sorted(files):
         h.update(f.encode())
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(csrc, f), encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

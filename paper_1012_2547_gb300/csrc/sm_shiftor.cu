@@ -9,27 +9,31 @@
 // and an occurrence ends at e iff bit m-1 of D is 1 (it starts at e-m+1).
 //
 // GB300 mapping
-//   * One warp per block; ~21 blocks per SM.  A warp claims work items
+//   * One warp per block; 20 blocks per SM.  A warp claims work items
 //     (query, item) from a device counter; an item is `sub_per_item`
 //     consecutive sub-tiles of 32 * 144 end positions whose bytes (plus the
 //     64 bytes before them) are staged HBM -> shared memory by one
 //     cp.async.bulk (TMA 1-D copy) on an mbarrier, double-buffered so the
 //     next sub-tile streams in while this one is scanned.
-//   * Lane l scans its own 144-byte segment from the empty state, one
-//     128-bit shared load per 16 bytes (144 is an odd multiple of 16, so the
-//     eight lanes of a quarter-warp hit eight different bank groups).  As
-//     the segment is at least m bytes long, the lane's final state is exact;
-//     lane l+1 takes it (shuffle) and extends only the partial matches it
-//     carries across the boundary, which usually dies within a byte or two.
-//     So no lane re-reads an m-1 byte halo.
+//   * Lane l scans its own 144-byte segment, one 128-bit shared load per 16
+//     bytes (144 is an odd multiple of 16, so the eight lanes of a
+//     quarter-warp hit eight different bank groups).  For m <= 16 the start
+//     state comes from a warm-up over the 8 or 16 bytes before the segment;
+//     otherwise the lane starts from the empty state (its final state is
+//     exact, as the segment is at least m bytes long) and lane l+1 takes it
+//     (shuffle) to extend only the partial matches it carries across the
+//     boundary, which usually die within a byte or two.
+//   * Byte tables with m <= 4 (m <= 6) take four (two) text bytes per state
+//     update through shifted copies of the table (see so_step4).
 //   * When bits m..m+15 of the state are spare (32-bit state and m <= 17,
 //     64-bit state and m <= 49), B[c] has ones there, so those bits carry
 //     the match flags of the last 16 positions: one shift per 16 bytes
 //     yields all 16 flags (variant "H").  Otherwise the state is ORed into
 //     an accumulator and a chunk with a match is re-scanned (variant "A").
-//   * Per-lane counts -> warp scan -> hits buffered per item in shared
-//     memory -> decoupled look-back across the items of the query ->
-//     coalesced copy to the output (capped by `cap`).
+//   * Per-lane counts -> warp scan -> hits kept per item in a spill area
+//     (a position list while sparse, flag and offset words of dense
+//     sub-tiles) -> decoupled look-back across the items of the query, one
+//     item later -> coalesced copy to the output (capped by `cap`).
 //
 // Positions are handled in a "virtual" frame shifted by o = text & 15, so
 // every staged sub-tile starts on a 16-byte boundary in memory.
@@ -68,8 +72,9 @@ constexpr uint32_t SO_MAX_SUB = 64;         // most sub-tiles per work item
 constexpr uint32_t SO_SUB_WORDS = 6;
 constexpr uint32_t SO_SUB_FLAGS = SO_SUB_WORDS * 32 * 4;
 // Spill area of one item: a list of item-relative positions (4 bytes per
-// hit: cheaper than flag words below about one hit per 32 bytes), then the
-// flag words of the sub-tiles that follow once the list is full.
+// hit: cheaper than a sub-tile's flag and offset words below SO_SUB_FLAGS / 4
+// hits), then the flag and offset words of the sub-tiles that follow once
+// the list is full or a sub-tile is denser than that.
 constexpr uint32_t SO_SPILL_POS = 4096;
 // (+256: with an item stride of exactly 64 KiB the packed kernel compiled
 // to 111 registers instead of 94.)

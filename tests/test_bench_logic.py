@@ -59,3 +59,10 @@ def test_committed_traffic_file_parses():
         assert fam in bench.KERNEL_NAMES and workload
         assert len(kv["source"]) == 16 and int(kv["source"], 16) >= 0
         assert float(kv["bytes_per_launch"]) > 0 and float(kv["inst_per_launch"]) > 0
+
+
+def test_source_hash_ignores_comments_and_whitespace():
+    src = 'int a = 1; // note\n/* block\n comment */ const char *s = "x // y";  int b;'
+    assert bench._code_only(src) == bench._code_only('int a = 1;\nconst char *s = "x // y"; int b; // other')
+    assert bench._code_only(src) != bench._code_only('int a = 2; const char *s = "x // y"; int b;')
+    assert bench._code_only(src) != bench._code_only('int a = 1; const char *s = "x / y"; int b;')
